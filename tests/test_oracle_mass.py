@@ -1,0 +1,82 @@
+"""Mass conservation of the oracle: solute plus precipitated solid
+(sum C + sum phi / V_m, Eq. solidFractionUpdate with the conserving sign),
+closed by the Dirichlet-cell and unpaid terms, through phase changes
+(Sec. 2.4).  The phase-change redistribution rules themselves are not fixed
+by the paper (parity unpinned beyond this invariant and the event checks)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2306_10794_gb300 import workloads
+
+
+def _invariant(L):
+    return L["solute"] + L["solid_over_vm"] + L["unpaid"] - L["dirichlet_in"] - L["open_in"]
+
+
+@pytest.mark.parametrize("c_init,c_eq,phi_solid,label", [
+    (3.0, 1.0, 1.0, "precipitation"),
+    (0.0, 1.0, 0.02, "dissolution"),
+])
+def test_closed_box_with_phase_change(c_init, c_eq, phi_solid, label):
+    shape = (14, 16, 18)
+    mask = workloads.sphere_pack(shape, 0.55, 2.0, 3.5, seed=7, periodic=(True, True, True))
+    rng = np.random.default_rng(5)
+    phi0 = np.where(mask == 1, phi_solid * rng.uniform(0.5, 1.0, shape), 0.0)
+    p = dict(dim=3, nx=18, ny=16, nz=14, flow_q=19, solute_q=7, bc=("periodic",) * 3, tau_flow=0.8,
+             magic_flow=3.0 / 16.0, tau_solute=0.9, k_r=0.2, c_eq=c_eq, c_init=c_init, molar_volume=0.3,
+             phase_change=1)
+    s = oracle.OracleSim(p, mask, phi_init=phi0)
+    I0 = _invariant(s.ledger())
+    s.step(150)
+    I1 = _invariant(s.ledger())
+    ev = s.events()
+    kinds = set(ev[:, 2].tolist())
+    want = oracle.EV_PRECIPITATE if label == "precipitation" else oracle.EV_DISSOLVE
+    assert want in kinds, "the case must exercise %s events" % label
+    assert abs(I1 - I0) <= 1e-12 * abs(I0)
+    # every cell class is consistent with the new geometry
+    cls = s.classes()
+    assert set(np.unique(cls)) <= {0, 1, 2}
+
+
+def test_dirichlet_ledger_closes_balance():
+    mask = workloads.reactive_wall_1d(6, 20)
+    p = dict(dim=2, nx=6, ny=20, flow_q=0, solute_q=9, bc=("periodic", "wall", "periodic"), tau_solute=0.9,
+             k_r=0.01, c_eq=0.0, c_dirichlet=1.0, c_init=0.2)
+    s = oracle.OracleSim(p, mask)
+    I0 = _invariant(s.ledger())
+    s.step(500)
+    L = s.ledger()
+    assert L["dirichlet_in"] > 0.0 and L["reacted"] < 0.0
+    assert abs(_invariant(L) - I0) < 1e-12 * abs(I0)
+
+
+def test_single_dissolution_event_by_hand():
+    """A boundary cell whose phi goes to <= 0 turns fluid with the mean
+    concentration of its fluid neighbours; its solid neighbours pay
+    V_m (C_init - C_b) - phi_b in equal shares (Sec. 2.4).  Expected values
+    are taken from a run without phase change, evaluated by hand."""
+    nx, ny, Vm = 5, 6, 0.4
+    mask = np.zeros((1, ny, nx), np.uint8)
+    mask[0, 0:2, :] = 1  # two solid rows; row 1 is the wet boundary row
+    phi0 = np.where(mask == 1, 1.0, 0.0)
+    phi0[0, 1, 2] = 1e-12  # this cell dissolves in the first step
+    p = dict(dim=2, nx=nx, ny=ny, flow_q=0, solute_q=5, bc=("periodic", "wall", "periodic"), tau_solute=1.0,
+             k_r=0.5, c_eq=1.0, c_init=0.0, molar_volume=Vm)
+    ref = oracle.OracleSim(dict(p, phase_change=0), mask, phi_init=phi0)
+    ref.step(1)
+    _, _, c_ref, phi_ref = ref.fields()
+    s = oracle.OracleSim(dict(p, phase_change=1), mask, phi_init=phi0)
+    s.step(1)
+    ev = s.events()
+    assert ev.tolist() == [[0, 2 + nx * 1, oracle.EV_DISSOLVE]]
+    cls = s.classes()[0]
+    assert cls[1, 2] == oracle.FLUID and cls[0, 2] == oracle.BOUND
+    _, _, c, phi = s.fields()
+    c_init = c_ref[0, 2, 2]  # the only fluid neighbour of (x=2, y=1)
+    assert c[0, 1, 2] == pytest.approx(c_init, rel=1e-14)
+    assert phi[0, 1, 2] == 0.0
+    Q = Vm * (c_init - c_ref[0, 1, 2]) - phi_ref[0, 1, 2]
+    paid = phi_ref[0, [1, 1, 0], [1, 3, 2]] - phi[0, [1, 1, 0], [1, 3, 2]]
+    assert np.allclose(paid, Q / 3.0, rtol=1e-12)

@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Throughput of the coupled LBM step with the general local reactive
+boundary condition on one GB300 (or N independent replicas under torchrun).
+
+Workload: 3D D3Q19 flow + D3Q7 solute in a 256x128x128 slab channel whose
+walls are tilted 30 degrees against the grid, plane-Poiseuille inflow at
+Re = 1, Pe = 10 (rest fraction), Da = 1, inlet c = 1, c_eq = 0.5, FP32
+populations with FP64 ledgers.  A step is one pass of the whole hot path:
+fluid stream-collide, reactive boundary condition + ledger + solid fraction
+on every wet boundary cell, and the precipitation-share gather.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the same workload instead (bounded per-step samples).
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled MLUPS and % of HBM roofline at stated accuracy vs FP64; adjoint/forward cost"
+BYTES_PER_FLUID_CELL = {"fp32": 2 * (19 + 7) * 4, "fp64": 2 * (19 + 7) * 8}
+L2_BYTES = 129e6
+
+
+def args_():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--theta", type=float, default=30.0)
+    ap.add_argument("--pe", type=float, default=10.0)
+    ap.add_argument("--da", type=float, default=1.0)
+    ap.add_argument("--size", type=str, default="256x128x128")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    return ap.parse_args()
+
+
+def workload(a):
+    from paper_2306_10794_gb300 import workloads
+
+    nx, ny, nz = (int(v) for v in a.size.split("x"))
+    p, mask, extra = workloads.case_channel(nx=nx, ny=ny, nz=nz, theta_deg=a.theta, Pe=a.pe, Da=a.da)
+    p["precision"] = a.precision
+    name = ("3D tilted channel %dx%dx%d, walls %g deg to the grid, D3Q19 TRT flow Re=1 + D3Q7 solute "
+            "Pe=%g Da=%g (rest fraction), c_in=1 c_eq=0.5, %s" % (nx, ny, nz, a.theta, a.pe, a.da, a.precision))
+    return p, mask, extra, name
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                c = [x.strip() for x in line.split(",")]
+                if len(c) >= 9:
+                    rows.append(c)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if re.match(r"^[0-9.]+$", r[1])]
+        mx = [float(r[2]) for r in rows if re.match(r"^[0-9.]+$", r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel_src_hash):
+    """DRAM bytes per launch of the fluid kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_fluid_channel.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None, None
+    m = re.search(r"source_sha256:\s*([0-9a-f]+)", txt)
+    t = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
+    if not m or not t or m.group(1) != kernel_src_hash:
+        return None, None
+    return float(t.group(1)), path
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("engine.cuh", "lattice.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2306_10794_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing
+# ---------------------------------------------------------------------------
+def oracle_mlups(p, mask, extra, budget_s, max_steps=None):
+    """Run the FP64 oracle on (a bounded x-slab of) the workload; returns
+    (MLUPS, cores, sample description, steps, seconds)."""
+    import numpy as np
+
+    import oracle
+
+    nz, ny, nx = mask.shape
+    # calibrate on a thin slab
+    q = dict(p)
+    cal_nx = min(nx, 8)
+    q["nx"] = cal_nx
+    o = oracle.OracleSim(q, np.ascontiguousarray(mask[:, :, :cal_nx]), **extra)
+    t0 = time.perf_counter()
+    o.step(1)
+    t_cal = time.perf_counter() - t0
+    o.close()
+    per_slab_col = t_cal / cal_nx
+    steps = max_steps or 1
+    sub_nx = max(4, min(nx, int(budget_s / max(steps * per_slab_col, 1e-9))))
+    q["nx"] = sub_nx
+    sub = np.ascontiguousarray(mask[:, :, :sub_nx])
+    o = oracle.OracleSim(q, sub, **extra)
+    fluid = int((sub == 0).sum())
+    done, t0 = 0, time.perf_counter()
+    while True:
+        o.step(1)
+        done += 1
+        el = time.perf_counter() - t0
+        if (max_steps and done >= max_steps) or (not max_steps and el >= budget_s):
+            break
+    o.close()
+    desc = "x-slab %dx%dx%d of the workload (first %d columns, inlet included), %d step(s)" % (
+        sub_nx, ny, nz, sub_nx, done)
+    return fluid * done / el / 1e6, 1, desc, done, el
+
+
+def reference_arm(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    p, mask, extra, name = workload(a)
+    K, W = max(1, a.steps), max(0, a.warmup)
+    # each step (warm-up and timed) is one oracle step on a bounded slab,
+    # sized so that the whole run stays around two minutes
+    per_step_budget = 110.0 / (K + W)
+    import numpy as np
+
+    import oracle
+
+    nz, ny, nx = mask.shape
+    q = dict(p)
+    cal_nx = min(nx, 8)
+    q["nx"] = cal_nx
+    o = oracle.OracleSim(q, np.ascontiguousarray(mask[:, :, :cal_nx]), **extra)
+    t0 = time.perf_counter()
+    o.step(1)
+    per_col = (time.perf_counter() - t0) / cal_nx
+    o.close()
+    sub_nx = max(4, min(nx, int(per_step_budget / max(per_col, 1e-9))))
+    q["nx"] = sub_nx
+    sub = np.ascontiguousarray(mask[:, :, :sub_nx])
+    o = oracle.OracleSim(q, sub, **extra)
+    fluid = int((sub == 0).sum())
+    o.step(W)
+    t0 = time.perf_counter()
+    o.step(K)
+    el = time.perf_counter() - t0
+    o.close()
+    v = fluid * K / el / 1e6
+    sample = "x-slab %dx%dx%d of the workload per step (oracle FP64, single thread)" % (sub_nx, ny, nz)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": a.gpus, "steps": K,
+            "warmup": W, "ms_per_step": el / K * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "sample": sample, "fluid_cells_per_step": fluid},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main():
+    a = args_()
+    if a.impl == "reference":
+        return reference_arm(a)
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_2306_10794_gb300 import _build, lbrbc
+
+    if rank == 0 or world == 1:
+        _build.build()
+    if dist:
+        dist.barrier()
+    p, mask, extra, name = workload(a)
+    K, W = max(1, a.steps), max(3, a.warmup)
+    stream = torch.cuda.current_stream()
+    sim = lbrbc.Sim(p, mask, **extra)
+    info = sim.info()
+    fluid = info["fluid_cells"]
+    sim.step(W, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(K, stream=stream.cuda_stream)
+    e1.record(stream)
+    barrier()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * fluid * K / (ms_max * 1e-3) / 1e6
+    sim.check()
+
+    # per-kernel durations, CUDA events on the launching stream (no graphs)
+    nprof = min(K, 2000)
+    kms, launches = sim.profile(nprof, stream=stream.cuda_stream)
+    sim.check()
+    bytes_launch = BYTES_PER_FLUID_CELL[a.precision] * fluid
+    peak, peak_kind = measured_peak()
+    achieved = bytes_launch / (kms[0] * 1e-3) / 1e9
+    khash = kernel_hash()
+    traffic, traffic_src = ncu_traffic(khash)
+    step_gbs = bytes_launch / (ms_max / K * 1e-3) / 1e9
+
+    # accuracy of this precision against the FP64 path (outside the timed region)
+    acc = None
+    if a.precision == "fp32" and not a.no_accuracy:
+        q = dict(p)
+        q["precision"] = "fp64"
+        s64 = lbrbc.Sim(q, mask, **extra)
+        s32 = lbrbc.Sim(p, mask, **extra)
+        s64.step(500)
+        s32.step(500)
+        u64, _, c64, _ = s64.fields()
+        u32, _, c32, _ = s32.fields()
+        rl2 = lambda x, y: float(np.sqrt(((x - y) ** 2).sum() / (y ** 2).sum()))
+        acc = {"steps": 500, "rel_l2_c": rl2(c32, c64), "rel_l2_u": rl2(u32, u64), "against": "FP64 CUDA path"}
+        s64.close()
+        s32.close()
+    sim.close()
+
+    # end to end through the C ABI with host buffers: create from the host
+    # mask, K steps, concentration and solid fraction back to the host
+    e2e = None
+    if not a.no_e2e:
+        barrier()
+        c_host = np.empty(mask.size)
+        phi_host = np.empty(mask.size)
+        t0 = time.perf_counter()
+        s2 = lbrbc.Sim(p, mask, **extra)
+        s2.step(K, stream=stream.cuda_stream)
+        lbrbc.lbrbc_fields(s2._h, None, None, c_host, phi_host)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        s2.close()
+        tt = torch.tensor([el], device="cuda", dtype=torch.float64)
+        if dist:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        h2d = mask.nbytes + extra["inlet_ux"].nbytes
+        d2h = c_host.nbytes + phi_host.nbytes
+        e2e = {"value": world * fluid * K / float(tt.item()) / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
+               "includes": "lbrbc_create from host mask + K steps + lbrbc_fields(c, phi) to host"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        v, cores, desc, n, el = oracle_mlups(p, mask, extra, budget_s=12.0)
+        cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if a.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": name, "grid": list(mask.shape[::-1]), "fluid_cells": fluid,
+                       "wet_boundary_cells": info["boundary_cells"], "parallelism": "replicas" if world > 1 else "1gpu",
+                       "l2_policy": "no flush: populations %.2f GB resident > L2 %.0f MB" % (
+                           (26 * (4 if a.precision == "fp32" else 8) * mask.size) / 1e9, L2_BYTES / 1e6)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_fluid (fluid-cell stream-collide, D3Q19 + D3Q7)",
+                         "bytes_per_launch": bytes_launch, "ms_per_launch": kms[0], "peak_kind": peak_kind,
+                         "traffic_source": traffic_src, "kernel_source_sha256": khash,
+                         "step_algorithmic_gbs": step_gbs},
+            "kernel_ms_per_step": {"fluid": kms[0], "boundary": kms[1], "fluid_ends": kms[2],
+                                   "phase_change": kms[3]},
+            "gpu_launches": int(launches * K),
+            "clocks": ck,
+            "accuracy": acc,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

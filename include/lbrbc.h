@@ -1,0 +1,189 @@
+/*
+ * lbrbc.h -- C ABI of the GB300 (sm_103a) library for the coupled lattice
+ * Boltzmann time step with the general local reactive boundary condition of
+ * Weinmiller et al., arXiv 2306.10794.
+ *
+ * One library call advances a flow lattice (D3Q19, or D2Q9 in 2D; BGK or TRT,
+ * Sec. 2.1, Eqs. fluid_BGK, fluid_Equilib, fluid_TRT) and a solute
+ * advection-diffusion lattice (D3Q7, or D2Q5 / D2Q9 in 2D; BGK or TRT with
+ * the rest-fraction weights, Eqs. solute_BGK, solute_equilibrium_function,
+ * solute_TRT, RestFraction, RestFractionCs2) by whole time steps.  Every
+ * solid-fluid link of the solute lattice carries the reactive boundary
+ * condition of Eq. general_RBC with k_i from Eq. k_i_S_New (or Eqs. k_i_S_Ve,
+ * k_i_S2, or its anti-bounce-back limit); the reacted mass feeds a per-cell
+ * solid fraction (Eq. solidFractionUpdate, adjacent growth, Sec. 2.4) whose
+ * thresholds phi <= 0 and phi >= 1 turn cells fluid or solid.
+ *
+ * Conventions
+ *   - Grids are indexed x fastest: cell (x, y, z) is entry x + nx*(y + ny*z)
+ *     of every caller array.  2D grids have nz = 1.
+ *   - Pointers marked "host" are read (or written) during the call only and
+ *     stay owned by the caller.  The library owns all device state of a
+ *     simulation; lbrbc_destroy releases it.
+ *   - Every entry point returns an lbrbc_status; on failure a message is
+ *     available from lbrbc_last_error (per simulation, or for the calling
+ *     thread when no simulation exists).  No exception crosses the ABI.
+ *   - The library runs its kernels on the CUDA stream given to lbrbc_step
+ *     (a cudaStream_t passed as void*).  NULL selects a stream owned by the
+ *     simulation and makes the call synchronous.
+ *   - There is no CPU fallback: a machine without a usable GPU gets
+ *     LBRBC_ERR_CUDA from lbrbc_create.
+ */
+#ifndef LBRBC_H
+#define LBRBC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbrbc_sim lbrbc_sim; /* opaque, owned by the library */
+
+typedef enum {
+    LBRBC_OK = 0,
+    LBRBC_ERR_ARG = 1,         /* invalid parameter or size                        */
+    LBRBC_ERR_CUDA = 2,        /* CUDA runtime error (message has the CUDA text)    */
+    LBRBC_ERR_NUMERIC = 3,     /* non-finite or non-positive density/concentration  */
+    LBRBC_ERR_TIMEOUT = 4,     /* reserved for bounded device waits                 */
+    LBRBC_ERR_STATE = 5,       /* capacity of an internal list exceeded             */
+    LBRBC_ERR_UNSUPPORTED = 6  /* lattice / option combination not built            */
+} lbrbc_status;
+
+/* Boundary treatment per axis.  OPEN is allowed on x only: x = 0 is a
+ * velocity inlet (moving-wall bounce-back for f, anti-bounce-back at
+ * c_inlet for g) and x = nx-1 a pressure outlet (anti-bounce-back at
+ * rho_outlet for f, anti-bounce-back at the cell's own previous
+ * concentration, i.e. zero gradient, for g).  WALL treats positions beyond the
+ * axis as inert solid (halfway bounce-back). */
+enum { LBRBC_PERIODIC = 0, LBRBC_WALL = 1, LBRBC_OPEN = 2 };
+
+/* k_i of Eq. general_RBC: Eq. k_i_S_New (default), Eq. k_i_S_Ve,
+ * Eq. k_i_S2, or k = infinity (anti-bounce-back, C_wall = C_eq). */
+enum { LBRBC_SCHEME_NEW = 0, LBRBC_SCHEME_VERHAEGHE = 1, LBRBC_SCHEME_PATEL_JU = 2, LBRBC_SCHEME_ANTI_BB = 3 };
+
+enum { LBRBC_FP32 = 0, LBRBC_FP64 = 1 };
+
+/* Cell codes of the mask given to lbrbc_create. */
+enum { LBRBC_CELL_FLUID = 0, LBRBC_CELL_REACTIVE = 1, LBRBC_CELL_DIRICHLET = 2 };
+
+/* Node classes reported by lbrbc_classes: a solid cell with a fluid
+ * neighbour along the solute lattice is a wet boundary node (BOUND). */
+enum { LBRBC_CLASS_FLUID = 0, LBRBC_CLASS_BOUND = 1, LBRBC_CLASS_SOLID = 2 };
+
+typedef struct {
+    int dim;                 /* 2 or 3                                              */
+    int nx, ny, nz;          /* grid size; nz = 1 when dim = 2                      */
+    int flow_q;              /* 19 (3D), 9 (2D) or 0 (no flow lattice: u = 0)        */
+    int solute_q;            /* 7 (3D), 5 or 9 (2D)                                  */
+    int bc[3];               /* LBRBC_PERIODIC / LBRBC_WALL / LBRBC_OPEN (x only)    */
+    int scheme;              /* LBRBC_SCHEME_*                                       */
+    int phase_change;        /* 1: cells change phase at phi <= 0 / phi >= 1         */
+    int precision;           /* LBRBC_FP32 (deviation storage) or LBRBC_FP64         */
+    int event_log_capacity;  /* phase-change events kept for lbrbc_events (0: none)  */
+    double tau_flow;         /* tau_NS (BGK) or tau_NS^+ (TRT); nu = (tau - 1/2)/3    */
+    double magic_flow;       /* Lambda of Eq. fluid_TRT_visc; < 0 selects BGK        */
+    double tau_solute;       /* tau_AD (BGK) or tau_AD^+ (TRT): D = cs^2 (tau - 1/2)  */
+    double magic_solute;     /* Lambda of Eq. solute_TRT_visc; < 0 selects BGK       */
+    double rest_fraction;    /* J0 of Eq. RestFraction (D2Q5/D3Q7); < 0: none        */
+    double k_r;              /* reaction rate coefficient (Eq. reactionRateBoundary) */
+    double c_eq;             /* equilibrium concentration                           */
+    double molar_volume;     /* V_m of Eq. solidFractionUpdate (a_m = dt = 1)        */
+    double c_init;           /* initial concentration (unless an init field given)   */
+    double rho_init;         /* initial density                                     */
+    double c_dirichlet;      /* concentration held by LBRBC_CELL_DIRICHLET cells     */
+    double c_inlet;          /* inlet concentration (OPEN x)                        */
+    double u_inlet;          /* plug inlet velocity when no inlet profile is given  */
+    double rho_outlet;       /* outlet density (OPEN x)                             */
+} lbrbc_params;
+
+/* Optional per-cell inputs; any pointer may be NULL.  All host pointers. */
+typedef struct {
+    const double *k_field;   /* N: per-voxel k_r replacing k_r on reactive cells    */
+    const double *c_init;    /* N: initial concentration                            */
+    const double *u_init;    /* 3N (x,y,z interleaved): initial velocity            */
+    const double *phi_init;  /* N: initial solid fraction (default 1 reactive, 0 else) */
+    const double *inlet_ux;  /* ny*nz: inlet velocity profile u_x(y, z)             */
+} lbrbc_init;
+
+/* Create a simulation (Sec. 2; problem statement of Sec. 2.3 / 2.4).
+ *   params    host, copied.  tau_* must exceed 1/2; rest_fraction < 1;
+ *             k_r, c_eq, molar_volume >= 0; Dirichlet and open boundaries
+ *             need a solute lattice.  Violations: LBRBC_ERR_ARG.
+ *   mask      host, nx*ny*nz bytes with LBRBC_CELL_* codes, copied.
+ *   init      host, optional (may be NULL).
+ *   out       receives the simulation handle.
+ * The populations start at equilibrium with rho_init, u_init and c_init. */
+lbrbc_status lbrbc_create(const lbrbc_params *params, const uint8_t *mask, const lbrbc_init *init,
+                          lbrbc_sim **out);
+
+/* Advance n >= 0 time steps (Sec. 2.1-2.4): stream-collide of both lattices,
+ * the reactive boundary condition on every solid-fluid link, the reacted-mass
+ * ledger, the solid-fraction update and, if enabled, the phase changes with
+ * the on-device rebuild of the boundary-link lists.  Kernels are enqueued on
+ * `stream` (cudaStream_t; NULL: the simulation's own stream, synchronous). */
+lbrbc_status lbrbc_step(lbrbc_sim *sim, int64_t n, void *stream);
+
+/* Moments of the current state (Eqs. fluid_BGK_visc, solute_diffu):
+ *   u    3N doubles (x,y,z interleaved), 0 outside fluid cells;
+ *   rho  N doubles, 0 outside fluid cells;
+ *   c    N doubles, concentration of fluid and boundary cells, 0 in the solid;
+ *   phi  N doubles, solid fraction of every cell.
+ * Any pointer may be NULL.  device = 1: the pointers are device memory of
+ * the simulation's GPU; device = 0: host memory.  Synchronises the stream
+ * given to the last lbrbc_step. */
+lbrbc_status lbrbc_fields(lbrbc_sim *sim, double *u, double *rho, double *c, double *phi, int device);
+
+/* Node class of every cell (LBRBC_CLASS_*), N bytes, host. */
+lbrbc_status lbrbc_classes(lbrbc_sim *sim, uint8_t *out);
+
+/* Mass balance (FP64, deterministic reduction order):
+ *   out[0] sum of c over fluid and boundary cells,
+ *   out[1] sum of phi / V_m over all cells,
+ *   out[2] dissolution charge that had no solid neighbour to pay it,
+ *   out[3] cumulative inflow through Dirichlet cells,
+ *   out[4] cumulative reacted mass (mass injected by reactive links),
+ *   out[5] completed time steps.
+ * With walls, periodic axes and Dirichlet cells (no OPEN axis),
+ * out[0] + out[1] + out[2] - out[3] is conserved to round-off.
+ * `out` is host memory with room for 6 doubles. */
+lbrbc_status lbrbc_mass_ledger(lbrbc_sim *sim, double *out);
+
+/* Phase-change events logged so far (up to event_log_capacity): on return
+ * *count holds the number logged; if step/node/kind are non-NULL the first
+ * min(*count, capacity) entries are written (host).  kind: 1 dissolution,
+ * 2 precipitation; node is the x-fastest cell index. */
+lbrbc_status lbrbc_events(lbrbc_sim *sim, int64_t *count, int64_t capacity, int64_t *step, int64_t *node,
+                          int32_t *kind);
+
+/* Measurement helper (no counterpart in the paper): advance n (1..4096)
+ * steps exactly as lbrbc_step does, but without CUDA graphs and with CUDA
+ * events recorded on `stream` around each kernel group; on return
+ * ms_out[0..3] hold the mean duration in milliseconds per step of the
+ * fluid-cell stream-collide kernel, the wet-boundary kernel (RBC, ledger,
+ * solid fraction), the precipitation-share gather and the phase-change
+ * group, and *launches (if non-NULL) the kernel launches per step.
+ * Synchronises the stream. */
+lbrbc_status lbrbc_profile_step(lbrbc_sim *sim, int64_t n, void *stream, double *ms_out, int64_t *launches);
+
+/* out[0] fluid cells, out[1] wet boundary cells at creation, out[2] kernel
+ * launches per time step (host memory, 3 entries). */
+lbrbc_status lbrbc_info(lbrbc_sim *sim, int64_t *out);
+
+/* Synchronise and report deferred device-side errors (non-finite state,
+ * list overflow).  Returns LBRBC_OK, LBRBC_ERR_NUMERIC or LBRBC_ERR_STATE. */
+lbrbc_status lbrbc_check(lbrbc_sim *sim);
+
+/* Message of the last failure of `sim`, or of the calling thread's last
+ * failed lbrbc_create when sim is NULL.  Never NULL. */
+const char *lbrbc_last_error(lbrbc_sim *sim);
+
+/* Release all device and host memory of the simulation.  NULL is a no-op. */
+void lbrbc_destroy(lbrbc_sim *sim);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBRBC_H */

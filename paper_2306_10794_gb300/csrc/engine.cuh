@@ -1,0 +1,1721 @@
+// Device engine of the coupled lattice Boltzmann step with the general local
+// reactive boundary condition (arXiv 2306.10794).  Templated over the storage
+// type T (float: deviation storage, double) and the flow / solute lattices.
+//
+// Storage ("AA pattern", one population array per lattice, in place):
+//   every population slot A[i][cell] of a padded dense grid (SoA, x fastest,
+//   rows padded to 32 cells, ghost layers on non-periodic axes).  After an
+//   even step the post-collision value f*_i(x) sits in A[opp(i)][x]; after
+//   an odd step in A[i][x + e_i], whatever lies at x + e_i (fluid, solid or
+//   ghost).  Writes never depend on the geometry; the boundary rules are
+//   applied when a node READS a population whose source x - e_i is inactive:
+//   the plain value there is its own f*_opp(i) (halfway bounce-back), which
+//   the open-boundary rules then modify.  Phase changes therefore never move
+//   populations: the next step simply reads with the new node classes.
+//
+// Per step: k_fluid (dense sweep, fluid cells: flow + solute), k_bound (the
+// compacted list of wet boundary cells: solute streaming, Eq. general_RBC on
+// every link to a fluid cell, ledger, collision with u = 0, solid-fraction
+// update), k_fend (fluid cells next to reactive boundary cells gather their
+// precipitation shares), and, with phase change, the event kernels that
+// apply Sec. 2.4 and rebuild the node words and both lists on the device.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lattice.cuh"
+#include "sim_iface.h"
+
+namespace lbrbc {
+
+enum : uint32_t { CLS_FLUID = 0, CLS_BOUND = 1, CLS_SOLID = 2 };
+enum : uint8_t { KIND_FLUID = 0, KIND_REACTIVE = 1, KIND_DIRICHLET = 2, KIND_OUTSIDE = 3 };
+enum : int { EV_DISSOLVE = 1, EV_PRECIPITATE = 2 };
+enum : int { ERR_NUMERIC = 1, ERR_OVERFLOW = 2 };
+
+// node word of a fluid cell: bits 0-1 class, bits FBIT.. "flow source
+// x - e_i is not fluid" for i = 1..QF-1, bits GBIT.. "solute source
+// x - e_i is inactive" for i = 1..QG-1.
+constexpr int FBIT = 2;
+constexpr int GBIT = 20;
+// word of a boundary-list entry: bits 0.. source inactive (i = 1..QG-1),
+// bits 8.. link towards a fluid cell (o = 1..QG-1), bit 16 Dirichlet cell.
+constexpr int BW_LINK = 8;
+constexpr uint32_t BW_DIRICHLET = 1u << 16;
+
+constexpr int FLUID_BLOCK = 128;
+constexpr int LIST_BLOCK = 256;
+constexpr int SCAN_CHUNK = 1024;
+
+struct Geo {
+    int nx, ny, nz;
+    int SX, SY, SZ;      // padded extents
+    int py, pz;          // ghost layers in y / z (0 when periodic)
+    int per_x, per_y, per_z, open_x;
+    long long OFF, NP;   // offset of the padded origin, slots per population
+    __host__ __device__ long long idx(int x, int y, int z) const {
+        return OFF + x + (long long)SX * ((long long)(y + py) + (long long)SY * (z + pz));
+    }
+};
+
+struct Nbr {
+    long long xp, xm, yp, ym, zp, zm;
+};
+
+__device__ __forceinline__ Nbr nbr_deltas(const Geo& g, int x, int y, int z) {
+    Nbr d;
+    const long long sy = g.SX, sz = (long long)g.SX * g.SY;
+    d.xp = (g.per_x && x == g.nx - 1) ? -(long long)(g.nx - 1) : 1;
+    d.xm = (g.per_x && x == 0) ? (long long)(g.nx - 1) : -1;
+    d.yp = (g.per_y && y == g.ny - 1) ? -(long long)(g.ny - 1) * sy : sy;
+    d.ym = (g.per_y && y == 0) ? (long long)(g.ny - 1) * sy : -sy;
+    d.zp = (g.per_z && z == g.nz - 1) ? -(long long)(g.nz - 1) * sz : sz;
+    d.zm = (g.per_z && z == 0) ? (long long)(g.nz - 1) * sz : -sz;
+    return d;
+}
+
+template <class L>
+__device__ __forceinline__ long long off(const Nbr& d, int i) {
+    return (L::cx(i) > 0 ? d.xp : (L::cx(i) < 0 ? d.xm : 0)) + (L::cy(i) > 0 ? d.yp : (L::cy(i) < 0 ? d.ym : 0)) +
+           (L::cz(i) > 0 ? d.zp : (L::cz(i) < 0 ? d.zm : 0));
+}
+
+// Is (x,y,z) + e inside the grid after periodic wrapping?  Writes the wrapped
+// coordinates.
+__device__ __forceinline__ bool wrap_inside(const Geo& g, int& x, int& y, int& z) {
+    if (x < 0 || x >= g.nx) {
+        if (!g.per_x) return false;
+        x = (x + g.nx) % g.nx;
+    }
+    if (y < 0 || y >= g.ny) {
+        if (!g.per_y) return false;
+        y = (y + g.ny) % g.ny;
+    }
+    if (z < 0 || z >= g.nz) {
+        if (!g.per_z) return false;
+        z = (z + g.nz) % g.nz;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void coords(const Geo& g, long long id, int& x, int& y, int& z) {
+    long long r = id - g.OFF;
+    x = (int)(r % g.SX);
+    long long t = r / g.SX;
+    y = (int)(t % g.SY) - g.py;
+    z = (int)(t / g.SY) - g.pz;
+}
+
+struct Phys {
+    double of_sym, of_anti;  // flow: 1/tau (symmetric), 1/tau^- (antisymmetric)
+    double og_sym, og_anti;  // solute: antisymmetric part relaxes with 1/tau_D
+    int trt_f, trt_g;
+    double gw0, gw1, gcs2;   // solute weights (rest / moving) and cs^2
+    double cref;             // reference concentration of the deviation storage
+    double c_inlet, rho_out, c_dir, c_eq, k_r, gamma, Vm, rho_init;
+    int scheme, phase_change;
+};
+
+template <typename T>
+struct Dev {
+    Geo geo;
+    T* F;                 // flow populations  (QF * NP)
+    T* G;                 // solute populations (QG * NP)
+    uint32_t* nw;         // node words (NP)
+    uint8_t* kind;        // cell kinds (NP)
+    double* phi;          // solid fraction (NP)
+    double* kfield;       // per-voxel k_r (NP) or null
+    double* inlet_ux;     // ny*nz
+    double* side;         // outlet: previous u (3 per cell) and C, 4*ny*nz
+    // wet boundary cells
+    int cap_b;
+    int* nb;
+    int* b_idx;
+    uint32_t* b_word;
+    long long* b_nbr;     // (QG-1) * cap_b
+    T* b_kappa;           // (QG-1) * cap_b
+    double* b_krate;      // cap_b or null
+    double* b_share;      // (QG-1) * cap_b
+    int* bmap;            // NP
+    // fluid cells receiving precipitation shares
+    int cap_f;
+    int* nf;
+    int* f_idx;
+    int* f_src;           // (QG-1) * cap_f, entry of the boundary cell at x - e_o
+    // phase-change events of the current step
+    int cap_e;
+    int* nev;
+    int* ev_node;
+    int* ev_kind;
+    double* ev_val;       // 3 * cap_e
+    double* ev_w;         // (QG-1) * cap_e
+    int* evidx;           // NP, -1 when not an event
+    // event log
+    long long cap_log;
+    long long* nlog;
+    long long* log_step;
+    long long* log_node;
+    int* log_kind;
+    long long* step;      // completed steps
+    double* acc;          // [0] reacted, [1] Dirichlet inflow, [2] unpaid
+    int* err;
+    // compaction scratch
+    int* blk;             // per chunk counts / offsets
+};
+
+template <class LG>
+__device__ __forceinline__ double gweight(const Phys& p, int i) {
+    if constexpr (LG::Q == 9) return LG::w(i);
+    else return i == 0 ? p.gw0 : p.gw1;
+}
+
+template <class LG>
+__device__ __forceinline__ double gcs2(const Phys& p) {
+    if constexpr (LG::Q == 9) return 1.0 / 3.0;
+    else return p.gcs2;
+}
+
+// ---------------------------------------------------------------------------
+// Collision helpers (deviation form: a_i stores value_i - w_i * ref).
+// ---------------------------------------------------------------------------
+template <class L, typename T>
+__device__ __forceinline__ void collide_flow(T (&f)[L::Q], T rho, T ux, T uy, T uz, const Phys& p) {
+    const T usq = ux * ux + uy * uy + uz * uz;
+    const T drho = rho - T(1);
+    if (!p.trt_f) {
+        const T om = T(p.of_sym);
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const T eu = T(L::cx(i)) * ux + T(L::cy(i)) * uy + T(L::cz(i)) * uz;
+            const T feq = T(L::w(i)) * (drho + rho * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * usq));
+            f[i] = f[i] - om * (f[i] - feq);
+        }
+    } else {
+        const T op = T(p.of_sym), om = T(p.of_anti);
+        {
+            const T feq = T(L::w(0)) * (drho - rho * T(1.5) * usq);
+            f[0] = f[0] - op * (f[0] - feq);
+        }
+#pragma unroll
+        for (int i = 1; i <= L::H; ++i) {
+            const int j = L::opp(i);
+            const T eu = T(L::cx(i)) * ux + T(L::cy(i)) * uy + T(L::cz(i)) * uz;
+            const T ep = T(L::w(i)) * (drho + rho * (T(4.5) * eu * eu - T(1.5) * usq));
+            const T em = T(L::w(i)) * rho * T(3) * eu;
+            const T fp = T(0.5) * (f[i] + f[j]), fm = T(0.5) * (f[i] - f[j]);
+            const T dp = op * (fp - ep), dm = om * (fm - em);
+            f[i] = f[i] - dp - dm;
+            f[j] = f[j] - dp + dm;
+        }
+    }
+}
+
+template <class L, typename T>
+__device__ __forceinline__ void collide_solute(T (&g)[L::Q], T C, T ux, T uy, T uz, const Phys& p) {
+    const T dc = C - T(p.cref);
+    const T ics2 = T(1.0 / gcs2<L>(p));
+    if (!p.trt_g) {
+        const T om = T(p.og_anti);
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const T eu = T(L::cx(i)) * ux + T(L::cy(i)) * uy + T(L::cz(i)) * uz;
+            const T w = T(gweight<L>(p, i));
+            const T geq = w * dc + w * C * eu * ics2;
+            g[i] = g[i] - om * (g[i] - geq);
+        }
+    } else {
+        const T os = T(p.og_sym), oa = T(p.og_anti);
+        g[0] = g[0] - os * (g[0] - T(gweight<L>(p, 0)) * dc);
+#pragma unroll
+        for (int i = 1; i <= L::H; ++i) {
+            const int j = L::opp(i);
+            const T eu = T(L::cx(i)) * ux + T(L::cy(i)) * uy + T(L::cz(i)) * uz;
+            const T w = T(gweight<L>(p, i));
+            const T ep = w * dc, em = w * C * eu * ics2;
+            const T gp = T(0.5) * (g[i] + g[j]), gm = T(0.5) * (g[i] - g[j]);
+            const T dp = os * (gp - ep), dm = oa * (gm - em);
+            g[i] = g[i] - dp - dm;
+            g[j] = g[j] - dp + dm;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fluid cells: stream (read side), boundary rules, moments, collide, write.
+// ---------------------------------------------------------------------------
+template <typename T, class LF, class LG, bool ODD>
+__global__ void __launch_bounds__(FLUID_BLOCK) k_fluid(const Dev<T> a, const Phys p) {
+    const Geo& g = a.geo;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    if (x >= g.nx) return;
+    const long long id = g.idx(x, y, z);
+    const uint32_t w = a.nw[id];
+    if ((w & 3u) != CLS_FLUID) return;
+    const Nbr d = nbr_deltas(g, x, y, z);
+    const long long NP = g.NP;
+    const bool inlet = g.open_x && x == 0;
+    const bool outlet = g.open_x && x == g.nx - 1;
+    const int face = y + g.ny * z;
+    T ux = T(0), uy = T(0), uz = T(0);
+    T rho = T(1);
+    if constexpr (LF::Q > 0) {
+        T f[LF::Q];
+        T uin = T(0), uo0 = T(0), uo1 = T(0), uo2 = T(0);
+        if (inlet) uin = T(a.inlet_ux[face]);
+        if (outlet) {
+            uo0 = T(a.side[4 * face + 0]);
+            uo1 = T(a.side[4 * face + 1]);
+            uo2 = T(a.side[4 * face + 2]);
+        }
+#pragma unroll
+        for (int i = 0; i < LF::Q; ++i) {
+            const bool wall = i > 0 && ((w >> (FBIT + i - 1)) & 1u);
+            T v;
+            if (ODD == wall) v = a.F[(long long)i * NP + id];
+            else v = a.F[(long long)LF::opp(i) * NP + id + off<LF>(d, LF::opp(i))];
+            if (wall) {
+                if (inlet && LF::cx(i) > 0) {
+                    // moving-wall bounce-back with the inlet velocity (rho_w = 1)
+                    v += T(6.0 * LF::w(i) * LF::cx(i)) * uin;
+                } else if (outlet && LF::cx(i) < 0) {
+                    // pressure anti-bounce-back at rho_out with the previous velocity
+                    const T eu = T(LF::cx(i)) * uo0 + T(LF::cy(i)) * uo1 + T(LF::cz(i)) * uo2;
+                    const T uq = uo0 * uo0 + uo1 * uo1 + uo2 * uo2;
+                    v = -v + T(2.0 * LF::w(i)) * (T(p.rho_out) * (T(1) + T(4.5) * eu * eu - T(1.5) * uq) - T(1));
+                }
+            }
+            f[i] = v;
+        }
+        T s = T(0), jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+        for (int i = 0; i < LF::Q; ++i) {
+            s += f[i];
+            if (LF::cx(i)) jx += T(LF::cx(i)) * f[i];
+            if (LF::cy(i)) jy += T(LF::cy(i)) * f[i];
+            if (LF::cz(i)) jz += T(LF::cz(i)) * f[i];
+        }
+        rho = T(1) + s;
+        const T inv = T(1) / rho;
+        ux = jx * inv;
+        uy = jy * inv;
+        uz = jz * inv;
+        collide_flow<LF, T>(f, rho, ux, uy, uz, p);
+#pragma unroll
+        for (int i = 0; i < LF::Q; ++i) {
+            if (ODD) a.F[(long long)i * NP + id + off<LF>(d, i)] = f[i];
+            else a.F[(long long)LF::opp(i) * NP + id] = f[i];
+        }
+    }
+    T gg[LG::Q];
+    const T co = outlet ? T(a.side[4 * face + 3]) : T(0);
+#pragma unroll
+    for (int i = 0; i < LG::Q; ++i) {
+        const bool wall = i > 0 && ((w >> (GBIT + i - 1)) & 1u);
+        T v;
+        if (ODD == wall) v = a.G[(long long)i * NP + id];
+        else v = a.G[(long long)LG::opp(i) * NP + id + off<LG>(d, LG::opp(i))];
+        if (wall) {
+            if (inlet && LG::cx(i) > 0) v = -v + T(2.0 * gweight<LG>(p, i)) * T(p.c_inlet - p.cref);
+            else if (outlet && LG::cx(i) < 0) v = -v + T(2.0 * gweight<LG>(p, i)) * (co - T(p.cref));
+        }
+        gg[i] = v;
+    }
+    T sc = T(0);
+#pragma unroll
+    for (int i = 0; i < LG::Q; ++i) sc += gg[i];
+    const T C = T(p.cref) + sc;
+    if (!(rho > T(0)) || !isfinite(C)) *a.err |= ERR_NUMERIC;
+    collide_solute<LG, T>(gg, C, ux, uy, uz, p);
+#pragma unroll
+    for (int i = 0; i < LG::Q; ++i) {
+        if (ODD) a.G[(long long)i * NP + id + off<LG>(d, i)] = gg[i];
+        else a.G[(long long)LG::opp(i) * NP + id] = gg[i];
+    }
+    if (outlet) {
+        a.side[4 * face + 0] = (double)ux;
+        a.side[4 * face + 1] = (double)uy;
+        a.side[4 * face + 2] = (double)uz;
+        a.side[4 * face + 3] = (double)C;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Event queue with warp-aggregated atomics.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void push_event(int* nev, int cap, int* ev_node, int* ev_kind, int* err, int node,
+                                           int kind) {
+    const unsigned mask = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(nev, __popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    const int pos = base + __popc(mask & ((1u << lane) - 1u));
+    if (pos < cap) {
+        ev_node[pos] = node;
+        ev_kind[pos] = kind;
+    } else {
+        atomicOr(err, ERR_OVERFLOW);
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Wet boundary cells (compacted list): solute stream, Eq. general_RBC on each
+// link to a fluid cell (all links from the streamed values), ledger
+// m_l = g_o(new) - g_o(streamed), collision with u = 0, Eq.
+// solidFractionUpdate (adjacent growth, conserving sign).
+// ---------------------------------------------------------------------------
+template <typename T, class LG, bool ODD>
+__global__ void __launch_bounds__(LIST_BLOCK) k_bound(const Dev<T> a, const Phys p) {
+    constexpr int Q = LG::Q;
+    const long long NP = a.geo.NP;
+    const int n = *a.nb;
+    double rsum = 0.0, dsum = 0.0;
+    const T cref = T(p.cref);
+    const T gam = T(p.gamma), ics2 = T(1.0 / gcs2<LG>(p));
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const long long b = a.b_idx[e];
+        const uint32_t bw = a.b_word[e];
+        T gp[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const bool inactive = i > 0 && ((bw >> (i - 1)) & 1u);
+            if (i == 0 || ODD == inactive) gp[i] = a.G[(long long)i * NP + b];
+            else gp[i] = a.G[(long long)LG::opp(i) * NP + a.b_nbr[(long long)(LG::opp(i) - 1) * a.cap_b + e]];
+        }
+        T g[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) g[i] = gp[i];
+        const bool dir = (bw & BW_DIRICHLET) != 0u;
+        const T kr = a.b_krate ? T(a.b_krate[e]) : T(p.k_r);
+        double m[Q];
+        double M = 0.0, S = 0.0;
+#pragma unroll
+        for (int o = 1; o < Q; ++o) {
+            m[o] = 0.0;
+            if (!((bw >> (BW_LINK + o - 1)) & 1u)) continue;
+            const T gt = gp[LG::opp(o)];
+            const T w2 = T(2.0 * gweight<LG>(p, o));
+            T val;
+            if (dir) {
+                val = -gt + w2 * T(p.c_dir - p.cref);  // anti-bounce-back, C_wall = c_dirichlet
+            } else {
+                const T kap = T(a.b_kappa[(long long)(o - 1) * a.cap_b + e]);
+                T k = T(0);
+                bool inf = false;
+                if (p.scheme == 0) k = gam * kr * kap * ics2;
+                else if (p.scheme == 1) k = kr * kap * ics2;
+                else if (p.scheme == 2) {
+                    if (kap > T(0)) k = gam * kr * ics2 / kap;
+                    else inf = true;
+                } else inf = true;
+                if (inf) val = -gt + w2 * (T(p.c_eq) - cref);
+                else {
+                    const T ik = T(1) / (T(1) + k);
+                    val = k * ik * w2 * (T(p.c_eq) - cref) + (T(1) - k) * ik * gt;
+                }
+            }
+            m[o] = (double)val - (double)gp[o];
+            g[o] = val;
+            M += m[o];
+            S += fabs(m[o]);
+        }
+        T sc = T(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) sc += g[i];
+        const T C = cref + sc;
+        if (!isfinite(C)) *a.err |= ERR_NUMERIC;
+        collide_solute<LG, T>(g, C, T(0), T(0), T(0), p);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (ODD) {
+                if (i == 0) a.G[b] = g[0];
+                else a.G[(long long)i * NP + a.b_nbr[(long long)(i - 1) * a.cap_b + e]] = g[i];
+            } else {
+                a.G[(long long)LG::opp(i) * NP + b] = g[i];
+            }
+        }
+        if (dir) {
+            dsum += M;
+#pragma unroll
+            for (int o = 1; o < Q; ++o) a.b_share[(long long)(o - 1) * a.cap_b + e] = 0.0;
+            continue;
+        }
+        rsum += M;
+        double ph = a.phi[b];
+        if (M > 0.0) {
+            ph -= p.Vm * M;
+            a.phi[b] = ph;
+        }
+#pragma unroll
+        for (int o = 1; o < Q; ++o)
+            a.b_share[(long long)(o - 1) * a.cap_b + e] = (M < 0.0) ? -p.Vm * M * fabs(m[o]) / S : 0.0;
+        if (p.phase_change && ph <= 0.0)
+            push_event(a.nev, a.cap_e, a.ev_node, a.ev_kind, a.err, (int)b, EV_DISSOLVE);
+    }
+    rsum = warp_sum(rsum);
+    dsum = warp_sum(dsum);
+    if ((threadIdx.x & 31) == 0 && (rsum != 0.0 || dsum != 0.0)) {
+        atomicAdd(&a.acc[0], rsum);
+        atomicAdd(&a.acc[1], dsum);
+    }
+}
+
+// Fluid cells at the ends of reactive links gather their precipitation
+// shares (fixed direction order) and test the phi >= 1 threshold.
+template <typename T, class LG>
+__global__ void __launch_bounds__(LIST_BLOCK) k_fend(const Dev<T> a, const Phys p) {
+    const int n = *a.nf;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const long long f = a.f_idx[e];
+        double acc = 0.0;
+#pragma unroll
+        for (int o = 1; o < LG::Q; ++o) {
+            const int s = a.f_src[(long long)(o - 1) * a.cap_f + e];
+            if (s >= 0) acc += a.b_share[(long long)(o - 1) * a.cap_b + s];
+        }
+        double ph = a.phi[f];
+        if (acc != 0.0) {
+            ph += acc;
+            a.phi[f] = ph;
+        }
+        if (p.phase_change && ph >= 1.0)
+            push_event(a.nev, a.cap_e, a.ev_node, a.ev_kind, a.err, (int)f, EV_PRECIPITATE);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Post-collision populations at their plain AA positions.
+// ---------------------------------------------------------------------------
+template <class L, typename T>
+__device__ __forceinline__ long long post_slot(long long id, const Nbr& d, int i, long long NP, bool lastodd) {
+    return lastodd ? (long long)i * NP + id + off<L>(d, i) : (long long)L::opp(i) * NP + id;
+}
+
+template <class L, typename T>
+__device__ __forceinline__ T post_sum(const T* A, long long id, const Nbr& d, long long NP, bool lastodd) {
+    T s = T(0);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) s += A[post_slot<L, T>(id, d, i, NP, lastodd)];
+    return s;
+}
+
+__device__ __forceinline__ Nbr nbr_of(const Geo& g, long long id) {
+    int x, y, z;
+    coords(g, id, x, y, z);
+    return nbr_deltas(g, x, y, z);
+}
+
+// Solid indicator for the wall normal: solid cells and positions beyond a
+// wall axis are 1; an open x axis is extended by clamping.
+__device__ __forceinline__ double solid_ind(const Geo& g, const uint8_t* kind, int x, int y, int z) {
+    if (x < 0 || x >= g.nx) {
+        if (g.per_x) x = (x + g.nx) % g.nx;
+        else if (g.open_x) x = x < 0 ? 0 : g.nx - 1;
+        else return 1.0;
+    }
+    if (y < 0 || y >= g.ny) {
+        if (g.per_y) y = (y + g.ny) % g.ny;
+        else return 1.0;
+    }
+    if (z < 0 || z >= g.nz) {
+        if (g.per_z) z = (z + g.nz) % g.nz;
+        else return 1.0;
+    }
+    return kind[g.idx(x, y, z)] != KIND_FLUID ? 1.0 : 0.0;
+}
+
+// Unit normal n = -grad s / |grad s| of the isotropic gradient
+// cs^-2 sum_i w_i s(x + e_i) e_i (D3Q19 / D2Q9 weights); false if |grad s|
+// is below 1e-12.
+template <int DIM>
+__device__ bool wall_normal(const Geo& g, const uint8_t* kind, int x, int y, int z, double n[3]) {
+    using L = typename NormalStencil<DIM>::L;
+    double gx = 0.0, gy = 0.0, gz = 0.0;
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) {
+        const double s = solid_ind(g, kind, x + L::cx(i), y + L::cy(i), z + L::cz(i));
+        gx += L::w(i) * s * L::cx(i) * 3.0;
+        gy += L::w(i) * s * L::cy(i) * 3.0;
+        gz += L::w(i) * s * L::cz(i) * 3.0;
+    }
+    const double len = sqrt(gx * gx + gy * gy + gz * gz);
+    if (len < 1e-12) {
+        n[0] = n[1] = n[2] = 0.0;
+        return false;
+    }
+    n[0] = -gx / len;
+    n[1] = -gy / len;
+    n[2] = -gz / len;
+    return true;
+}
+
+// Class of an in-grid cell from the kinds: fluid, or solid with / without a
+// fluid neighbour along the solute lattice.
+template <class LG>
+__device__ uint32_t class_of(const Geo& g, const uint8_t* kind, int x, int y, int z) {
+    const uint8_t k = kind[g.idx(x, y, z)];
+    if (k == KIND_FLUID) return CLS_FLUID;
+#pragma unroll
+    for (int o = 1; o < LG::Q; ++o) {
+        int xx = x + LG::cx(o), yy = y + LG::cy(o), zz = z + LG::cz(o);
+        if (wrap_inside(g, xx, yy, zz) && kind[g.idx(xx, yy, zz)] == KIND_FLUID) return CLS_BOUND;
+    }
+    return CLS_SOLID;
+}
+
+template <class LG>
+__device__ __forceinline__ uint32_t class_at(const Geo& g, const uint8_t* kind, int x, int y, int z) {
+    if (!wrap_inside(g, x, y, z)) return CLS_SOLID;
+    return class_of<LG>(g, kind, x, y, z);
+}
+
+// ---------------------------------------------------------------------------
+// Phase change (Sec. 2.4), applied to all cells that crossed a threshold in
+// this step at once.  Every cell that receives something gathers it in a
+// fixed direction order, so the result does not depend on thread timing.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_ev_mark(const Dev<T> a) {
+    const int n = *a.nev;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n && e < a.cap_e; e += gridDim.x * blockDim.x) {
+        const int node = a.ev_node[e];
+        const int kd = a.ev_kind[e];
+        a.evidx[node] = e;
+        a.kind[node] = kd == EV_DISSOLVE ? KIND_FLUID : KIND_REACTIVE;
+        if (a.cap_log > 0) {
+            const long long pos = atomicAdd((unsigned long long*)a.nlog, 1ull);
+            if (pos < a.cap_log) {
+                int x, y, z;
+                coords(a.geo, node, x, y, z);
+                a.log_step[pos] = *a.step;
+                a.log_node[pos] = x + (long long)a.geo.nx * (y + (long long)a.geo.ny * z);
+                a.log_kind[pos] = kd;
+            }
+        }
+    }
+}
+
+template <typename T, class LF, class LG>
+__global__ void k_ev_compute(const Dev<T> a, const Phys p, int lastodd) {
+    const int n = min(*a.nev, a.cap_e);
+    const Geo& g = a.geo;
+    const long long NP = g.NP;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const long long id = a.ev_node[e];
+        int x, y, z;
+        coords(g, id, x, y, z);
+        const Nbr d = nbr_deltas(g, x, y, z);
+        const double Cself = p.cref + (double)post_sum<LG, T>(a.G, id, d, NP, lastodd);
+        if (a.ev_kind[e] == EV_DISSOLVE) {
+            double sc = 0.0, sr = 0.0;
+            int nfl = 0, ns = 0;
+#pragma unroll
+            for (int o = 1; o < LG::Q; ++o) {
+                int xx = x + LG::cx(o), yy = y + LG::cy(o), zz = z + LG::cz(o);
+                if (!wrap_inside(g, xx, yy, zz)) continue;
+                const long long nb = g.idx(xx, yy, zz);
+                if ((a.nw[nb] & 3u) == CLS_FLUID) {
+                    const Nbr dn = nbr_deltas(g, xx, yy, zz);
+                    sc += p.cref + (double)post_sum<LG, T>(a.G, nb, dn, NP, lastodd);
+                    if constexpr (LF::Q > 0) sr += 1.0 + (double)post_sum<LF, T>(a.F, nb, dn, NP, lastodd);
+                    else sr += 1.0;
+                    nfl++;
+                }
+                if (a.kind[nb] == KIND_REACTIVE) ns++;
+            }
+            const double cinit = nfl ? sc / nfl : Cself;
+            const double rinit = nfl ? sr / nfl : p.rho_init;
+            const double Q = p.Vm * (cinit - Cself) - a.phi[id];
+            a.ev_val[e] = cinit;
+            a.ev_val[a.cap_e + e] = rinit;
+            a.ev_val[2 * a.cap_e + e] = ns ? Q / ns : 0.0;
+            if (!ns) atomicAdd(&a.acc[2], -Q / p.Vm);
+        } else {
+            const double phic = a.phi[id] + p.Vm * Cself;
+            const double excess = phic - 1.0;
+            double nrm[3];
+            const bool ok = wall_normal<LG::DIM>(g, a.kind, x, y, z, nrm);
+            double kap[LG::Q];
+            double sk = 0.0;
+            int nfl = 0;
+#pragma unroll
+            for (int o = 1; o < LG::Q; ++o) {
+                kap[o] = 0.0;
+                int xx = x + LG::cx(o), yy = y + LG::cy(o), zz = z + LG::cz(o);
+                if (!wrap_inside(g, xx, yy, zz)) continue;
+                if (a.kind[g.idx(xx, yy, zz)] != KIND_FLUID) continue;
+                double kk = 1.0;
+                if (ok) {
+                    kk = LG::cx(o) * nrm[0] + LG::cy(o) * nrm[1] + LG::cz(o) * nrm[2];
+                    kk = kk > 0.0 ? kk : 0.0;
+                }
+                kap[o] = kk;
+                sk += kk;
+                nfl++;
+            }
+#pragma unroll
+            for (int o = 1; o < LG::Q; ++o) {
+                int xx = x + LG::cx(o), yy = y + LG::cy(o), zz = z + LG::cz(o);
+                bool fl = wrap_inside(g, xx, yy, zz) && a.kind[g.idx(xx, yy, zz)] == KIND_FLUID;
+                double share = fl ? (sk > 0.0 ? kap[o] / sk : 1.0 / nfl) : 0.0;
+                a.ev_w[(long long)(o - 1) * a.cap_e + e] = nfl ? excess / p.Vm * share : 0.0;
+            }
+            a.ev_val[e] = nfl ? 1.0 : phic;
+        }
+    }
+}
+
+template <typename T, class LF, class LG>
+__global__ void k_ev_apply_self(const Dev<T> a, const Phys p, int lastodd) {
+    const int n = min(*a.nev, a.cap_e);
+    const Geo& g = a.geo;
+    const long long NP = g.NP;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const long long id = a.ev_node[e];
+        const Nbr d = nbr_of(g, id);
+        if (a.ev_kind[e] == EV_DISSOLVE) {
+            const double cinit = a.ev_val[e], rinit = a.ev_val[a.cap_e + e];
+#pragma unroll
+            for (int i = 0; i < LG::Q; ++i)
+                a.G[post_slot<LG, T>(id, d, i, NP, lastodd)] = T(gweight<LG>(p, i) * (cinit - p.cref));
+            if constexpr (LF::Q > 0) {
+#pragma unroll
+                for (int i = 0; i < LF::Q; ++i) a.F[post_slot<LF, T>(id, d, i, NP, lastodd)] = T(LF::w(i) * (rinit - 1.0));
+            }
+            a.phi[id] = 0.0;
+        } else {
+#pragma unroll
+            for (int i = 0; i < LG::Q; ++i)
+                a.G[post_slot<LG, T>(id, d, i, NP, lastodd)] = T(-gweight<LG>(p, i) * p.cref);
+            a.phi[id] = a.ev_val[e];
+        }
+    }
+}
+
+// One thread per (event, direction); the cell x_e + e_o is handled by the
+// event found first when scanning its own neighbours in direction order.
+template <typename T, class LG>
+__global__ void k_ev_neighbours(const Dev<T> a, const Phys p, int lastodd) {
+    constexpr int NQ = LG::Q - 1;
+    const int n = min(*a.nev, a.cap_e);
+    const Geo& g = a.geo;
+    const long long NP = g.NP;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)n * NQ;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int e = (int)(t / NQ), o = 1 + (int)(t % NQ);
+        const long long src = a.ev_node[e];
+        int x, y, z;
+        coords(g, src, x, y, z);
+        x += LG::cx(o);
+        y += LG::cy(o);
+        z += LG::cz(o);
+        // note: LG::cx(o) with a run-time o; fine outside the hot path
+        if (!wrap_inside(g, x, y, z)) continue;
+        const long long tgt = g.idx(x, y, z);
+        int first = -1;
+        for (int q = 1; q < LG::Q; ++q) {
+            int xx = x + LG::cx(q), yy = y + LG::cy(q), zz = z + LG::cz(q);
+            if (!wrap_inside(g, xx, yy, zz)) continue;
+            if (a.evidx[g.idx(xx, yy, zz)] >= 0) {
+                first = q;
+                break;
+            }
+        }
+        if (first != LG::opp(o)) continue;
+        double charge = 0.0, dC = 0.0;
+        const uint8_t kt = a.kind[tgt];
+        for (int q = 1; q < LG::Q; ++q) {
+            int xx = x + LG::cx(q), yy = y + LG::cy(q), zz = z + LG::cz(q);
+            if (!wrap_inside(g, xx, yy, zz)) continue;
+            const int ee = a.evidx[g.idx(xx, yy, zz)];
+            if (ee < 0) continue;
+            if (a.ev_kind[ee] == EV_DISSOLVE && kt == KIND_REACTIVE) charge += a.ev_val[2 * a.cap_e + ee];
+            if (a.ev_kind[ee] == EV_PRECIPITATE && kt == KIND_FLUID)
+                dC += a.ev_w[(long long)(LG::opp(q) - 1) * a.cap_e + ee];
+        }
+        if (charge != 0.0) a.phi[tgt] -= charge;
+        if (dC != 0.0) {
+            const Nbr d = nbr_deltas(g, x, y, z);
+            for (int i = 0; i < LG::Q; ++i) {
+                const long long s = post_slot<LG, T>(tgt, d, i, NP, lastodd);
+                a.G[s] = T((double)a.G[s] + gweight<LG>(p, i) * dC);
+            }
+        }
+    }
+}
+
+// New classes and node words from the kinds (whole grid); boundary cells
+// that lost their last fluid neighbour convert their solute into phi, solid
+// cells that gained one start empty.
+template <typename T, class LF, class LG>
+__global__ void k_reclassify(const Dev<T> a, const Phys p, int lastodd, int force) {
+    if (!force && *a.nev == 0) return;
+    const Geo& g = a.geo;
+    const long long NP = g.NP;
+    const long long total = (long long)g.nx * g.ny * g.nz;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(t % g.nx);
+        const int y = (int)((t / g.nx) % g.ny);
+        const int z = (int)(t / ((long long)g.nx * g.ny));
+        const long long id = g.idx(x, y, z);
+        const uint32_t cls = class_of<LG>(g, a.kind, x, y, z);
+        const uint32_t old = a.nw[id] & 3u;
+        if (!force && old != cls && a.evidx[id] < 0) {
+            const Nbr d = nbr_deltas(g, x, y, z);
+            if (old == CLS_BOUND && cls == CLS_SOLID) {
+                const double C = p.cref + (double)post_sum<LG, T>(a.G, id, d, NP, lastodd);
+                if (a.kind[id] == KIND_REACTIVE) a.phi[id] += p.Vm * C;
+                else atomicAdd(&a.acc[1], -C);
+            }
+            if (cls != CLS_FLUID) {
+#pragma unroll
+                for (int i = 0; i < LG::Q; ++i)
+                    a.G[post_slot<LG, T>(id, d, i, NP, lastodd)] = T(-gweight<LG>(p, i) * p.cref);
+            }
+        }
+        uint32_t w = cls;
+        if (cls == CLS_FLUID) {
+            if constexpr (LF::Q > 0) {
+#pragma unroll
+                for (int i = 1; i < LF::Q; ++i) {
+                    int xx = x - LF::cx(i), yy = y - LF::cy(i), zz = z - LF::cz(i);
+                    if (class_at<LG>(g, a.kind, xx, yy, zz) != CLS_FLUID) w |= 1u << (FBIT + i - 1);
+                }
+            }
+#pragma unroll
+            for (int i = 1; i < LG::Q; ++i) {
+                int xx = x - LG::cx(i), yy = y - LG::cy(i), zz = z - LG::cz(i);
+                if (class_at<LG>(g, a.kind, xx, yy, zz) == CLS_SOLID) w |= 1u << (GBIT + i - 1);
+            }
+        }
+        a.nw[id] = w;
+    }
+}
+
+// Stream compaction of the wet boundary cells (order = cell index).
+// Pass 1: counts per chunk of SCAN_CHUNK cells.
+template <typename T, class LG>
+__global__ void k_count(const Dev<T> a, int which, int force) {
+    if (!force && *a.nev == 0) return;
+    const Geo& g = a.geo;
+    const long long total = (long long)g.nx * g.ny * g.nz;
+    const long long chunk = blockIdx.x;
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    int local = 0;
+    for (long long t = chunk * SCAN_CHUNK + threadIdx.x; t < min(total, (chunk + 1) * SCAN_CHUNK); t += blockDim.x) {
+        const int x = (int)(t % g.nx);
+        const int y = (int)((t / g.nx) % g.ny);
+        const int z = (int)(t / ((long long)g.nx * g.ny));
+        const long long id = g.idx(x, y, z);
+        const uint32_t cls = a.nw[id] & 3u;
+        if (which == 0) local += cls == CLS_BOUND;
+        else if (cls == CLS_FLUID) {
+#pragma unroll
+            for (int o = 1; o < LG::Q; ++o) {
+                int xx = x - LG::cx(o), yy = y - LG::cy(o), zz = z - LG::cz(o);
+                if (!wrap_inside(g, xx, yy, zz)) continue;
+                const long long nb = g.idx(xx, yy, zz);
+                if ((a.nw[nb] & 3u) == CLS_BOUND && a.kind[nb] == KIND_REACTIVE) {
+                    local++;
+                    break;
+                }
+            }
+        }
+    }
+    atomicAdd(&cnt, local);
+    __syncthreads();
+    if (threadIdx.x == 0) a.blk[chunk] = cnt;
+}
+
+// Pass 2: exclusive scan of the chunk counts (one block); total -> *count.
+template <typename T>
+__global__ void k_scan(const Dev<T> a, int nchunks, int which, int force) {
+    if (!force && *a.nev == 0) return;
+    __shared__ int part[1024];
+    const int per = (nchunks + blockDim.x - 1) / blockDim.x;
+    const int lo = threadIdx.x * per, hi = min(nchunks, lo + per);
+    int s = 0;
+    for (int c = lo; c < hi; ++c) s += a.blk[c];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int k = 0; k < (int)blockDim.x; ++k) {
+            const int v = part[k];
+            part[k] = run;
+            run += v;
+        }
+        const int cap = which == 0 ? a.cap_b : a.cap_f;
+        if (run > cap) atomicOr(a.err, ERR_OVERFLOW);
+        *(which == 0 ? a.nb : a.nf) = min(run, cap);
+    }
+    __syncthreads();
+    int run = part[threadIdx.x];
+    for (int c = lo; c < hi; ++c) {
+        const int v = a.blk[c];
+        a.blk[c] = run;
+        run += v;
+    }
+}
+
+// Pass 3: write the entries in cell order.
+template <typename T, class LG>
+__global__ void k_write_lists(const Dev<T> a, const Phys p, int which, int force) {
+    if (!force && *a.nev == 0) return;
+    const Geo& g = a.geo;
+    const long long total = (long long)g.nx * g.ny * g.nz;
+    const long long chunk = blockIdx.x;
+    __shared__ int warp_tot[32];
+    __shared__ int base_s;
+    if (threadIdx.x == 0) base_s = a.blk[chunk];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw_ = blockDim.x >> 5;
+    for (long long t0 = chunk * SCAN_CHUNK; t0 < min(total, (chunk + 1) * SCAN_CHUNK); t0 += blockDim.x) {
+        const long long t = t0 + threadIdx.x;
+        bool sel = false;
+        int x = 0, y = 0, z = 0;
+        long long id = 0;
+        int src[LG::Q];
+        if (t < min(total, (chunk + 1) * SCAN_CHUNK)) {
+            x = (int)(t % g.nx);
+            y = (int)((t / g.nx) % g.ny);
+            z = (int)(t / ((long long)g.nx * g.ny));
+            id = g.idx(x, y, z);
+            const uint32_t cls = a.nw[id] & 3u;
+            if (which == 0) {
+                sel = cls == CLS_BOUND;
+                a.bmap[id] = -1;
+            } else if (cls == CLS_FLUID) {
+#pragma unroll
+                for (int o = 1; o < LG::Q; ++o) {
+                    src[o] = -1;
+                    int xx = x - LG::cx(o), yy = y - LG::cy(o), zz = z - LG::cz(o);
+                    if (!wrap_inside(g, xx, yy, zz)) continue;
+                    const long long nb = g.idx(xx, yy, zz);
+                    if ((a.nw[nb] & 3u) == CLS_BOUND && a.kind[nb] == KIND_REACTIVE) {
+                        src[o] = a.bmap[nb];
+                        sel = true;
+                    }
+                }
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, sel);
+        if (lane == 0) warp_tot[wid] = __popc(bal);
+        __syncthreads();
+        int woff = 0, tot = 0;
+        for (int k = 0; k < nw_; ++k) {
+            if (k < wid) woff += warp_tot[k];
+            tot += warp_tot[k];
+        }
+        const int pos = base_s + woff + __popc(bal & ((1u << lane) - 1u));
+        if (sel) {
+            if (which == 0 && pos < a.cap_b) {
+                a.b_idx[pos] = (int)id;
+                a.bmap[id] = pos;
+                uint32_t bw = 0;
+                const uint8_t kd = a.kind[id];
+                if (kd == KIND_DIRICHLET) bw |= BW_DIRICHLET;
+                double nrm[3];
+                const bool ok = wall_normal<LG::DIM>(g, a.kind, x, y, z, nrm);
+                const Nbr d = nbr_deltas(g, x, y, z);
+#pragma unroll
+                for (int o = 1; o < LG::Q; ++o) {
+                    a.b_nbr[(long long)(o - 1) * a.cap_b + pos] = id + off<LG>(d, o);
+                    int xs = x - LG::cx(o), ys = y - LG::cy(o), zs = z - LG::cz(o);
+                    if (class_at<LG>(g, a.kind, xs, ys, zs) == CLS_SOLID) bw |= 1u << (o - 1);
+                    int xf = x + LG::cx(o), yf = y + LG::cy(o), zf = z + LG::cz(o);
+                    T kap = T(0);
+                    if (wrap_inside(g, xf, yf, zf) && a.kind[g.idx(xf, yf, zf)] == KIND_FLUID) {
+                        bw |= 1u << (BW_LINK + o - 1);
+                        double kk = 1.0;
+                        if (ok) {
+                            kk = LG::cx(o) * nrm[0] + LG::cy(o) * nrm[1] + LG::cz(o) * nrm[2];
+                            kk = kk > 0.0 ? kk : 0.0;
+                        }
+                        kap = T(kk);
+                    }
+                    a.b_kappa[(long long)(o - 1) * a.cap_b + pos] = kap;
+                }
+                a.b_word[pos] = bw;
+                if (a.b_krate) a.b_krate[pos] = a.kfield ? a.kfield[id] : p.k_r;
+            } else if (which == 1 && pos < a.cap_f) {
+                a.f_idx[pos] = (int)id;
+#pragma unroll
+                for (int o = 1; o < LG::Q; ++o) a.f_src[(long long)(o - 1) * a.cap_f + pos] = src[o];
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) base_s += tot;
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void k_ev_reset(const Dev<T> a) {
+    const int n = min(*a.nev, a.cap_e);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) a.evidx[a.ev_node[e]] = -1;
+}
+
+template <typename T>
+__global__ void k_step_end(const Dev<T> a) {
+    *a.nev = 0;
+    *a.step += 1;
+}
+
+// Initial state: equilibrium populations written as an odd step would write
+// them, so the first step (even) reads them as streamed values.
+template <typename T, class LF, class LG>
+__global__ void k_init(const Dev<T> a, const Phys p, const double* __restrict__ c0, const double* __restrict__ u0) {
+    const Geo& g = a.geo;
+    const long long NP = g.NP;
+    const long long total = (long long)g.nx * g.ny * g.nz;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(t % g.nx);
+        const int y = (int)((t / g.nx) % g.ny);
+        const int z = (int)(t / ((long long)g.nx * g.ny));
+        const long long id = g.idx(x, y, z);
+        const uint32_t cls = a.nw[id] & 3u;
+        const Nbr d = nbr_deltas(g, x, y, z);
+        double ux = 0.0, uy = 0.0, uz = 0.0;
+        if (cls == CLS_FLUID && u0) {
+            ux = u0[3 * t];
+            uy = u0[3 * t + 1];
+            uz = u0[3 * t + 2];
+        }
+        const double C = c0[t];
+        if constexpr (LF::Q > 0) {
+            if (cls == CLS_FLUID) {
+                const double rho = p.rho_init, usq = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+                for (int i = 0; i < LF::Q; ++i) {
+                    const double eu = LF::cx(i) * ux + LF::cy(i) * uy + LF::cz(i) * uz;
+                    const double feq = LF::w(i) * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
+                    a.F[(long long)i * NP + id + off<LF>(d, i)] = T(feq - LF::w(i));
+                }
+            }
+        }
+        if (cls != CLS_SOLID) {
+            const double ics2 = 1.0 / gcs2<LG>(p);
+#pragma unroll
+            for (int i = 0; i < LG::Q; ++i) {
+                const double eu = LG::cx(i) * ux + LG::cy(i) * uy + LG::cz(i) * uz;
+                const double w = gweight<LG>(p, i);
+                a.G[(long long)i * NP + id + off<LG>(d, i)] = T(C * w * (1.0 + eu * ics2) - w * p.cref);
+            }
+        }
+        if (g.open_x && x == g.nx - 1) {
+            const int face = y + g.ny * z;
+            a.side[4 * face + 0] = ux;
+            a.side[4 * face + 1] = uy;
+            a.side[4 * face + 2] = uz;
+            a.side[4 * face + 3] = C;
+        }
+    }
+}
+
+// Moments of the current state into caller-layout FP64 arrays.
+template <typename T, class LF, class LG>
+__global__ void k_fields(const Dev<T> a, const Phys p, int lastodd, double* u, double* rho, double* c, double* phi) {
+    const Geo& g = a.geo;
+    const long long NP = g.NP;
+    const long long total = (long long)g.nx * g.ny * g.nz;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(t % g.nx);
+        const int y = (int)((t / g.nx) % g.ny);
+        const int z = (int)(t / ((long long)g.nx * g.ny));
+        const long long id = g.idx(x, y, z);
+        const uint32_t cls = a.nw[id] & 3u;
+        const Nbr d = nbr_deltas(g, x, y, z);
+        double r = 0.0, jx = 0.0, jy = 0.0, jz = 0.0, C = 0.0;
+        if constexpr (LF::Q > 0) {
+            if (cls == CLS_FLUID) {
+                double s = 0.0;
+#pragma unroll
+                for (int i = 0; i < LF::Q; ++i) {
+                    const double v = (double)a.F[post_slot<LF, T>(id, d, i, NP, lastodd)];
+                    s += v;
+                    jx += LF::cx(i) * v;
+                    jy += LF::cy(i) * v;
+                    jz += LF::cz(i) * v;
+                }
+                r = 1.0 + s;
+                jx /= r;
+                jy /= r;
+                jz /= r;
+            }
+        }
+        if (cls != CLS_SOLID) C = p.cref + (double)post_sum<LG, T>(a.G, id, d, NP, lastodd);
+        if (u) {
+            u[3 * t] = jx;
+            u[3 * t + 1] = jy;
+            u[3 * t + 2] = jz;
+        }
+        if (rho) rho[t] = r;
+        if (c) c[t] = C;
+        if (phi) phi[t] = a.phi[id];
+    }
+}
+
+template <typename T>
+__global__ void k_classes(const Dev<T> a, uint8_t* out) {
+    const Geo& g = a.geo;
+    const long long total = (long long)g.nx * g.ny * g.nz;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(t % g.nx);
+        const int y = (int)((t / g.nx) % g.ny);
+        const int z = (int)(t / ((long long)g.nx * g.ny));
+        out[t] = (uint8_t)(a.nw[g.idx(x, y, z)] & 3u);
+    }
+}
+
+// Deterministic two-pass reduction: per-block partial sums (fixed block
+// partition and tree order), then one block sums the partials in order.
+constexpr int RED_BLOCK = 256;
+template <typename T, class LG>
+__global__ void __launch_bounds__(RED_BLOCK) k_reduce_partial(const Dev<T> a, const Phys p, int lastodd, double* part) {
+    const Geo& g = a.geo;
+    const long long NP = g.NP;
+    const long long total = (long long)g.nx * g.ny * g.nz;
+    double sc = 0.0, sp = 0.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(t % g.nx);
+        const int y = (int)((t / g.nx) % g.ny);
+        const int z = (int)(t / ((long long)g.nx * g.ny));
+        const long long id = g.idx(x, y, z);
+        if ((a.nw[id] & 3u) != CLS_SOLID) {
+            const Nbr d = nbr_deltas(g, x, y, z);
+            double s = 0.0;
+#pragma unroll
+            for (int i = 0; i < LG::Q; ++i) s += (double)a.G[post_slot<LG, T>(id, d, i, NP, lastodd)];
+            sc += p.cref + s;
+        }
+        sp += a.phi[id];
+    }
+    __shared__ double s1[RED_BLOCK], s2[RED_BLOCK];
+    s1[threadIdx.x] = sc;
+    s2[threadIdx.x] = sp;
+    __syncthreads();
+    for (int k = RED_BLOCK / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) {
+            s1[threadIdx.x] += s1[threadIdx.x + k];
+            s2[threadIdx.x] += s2[threadIdx.x + k];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = s1[0];
+        part[2 * blockIdx.x + 1] = s2[0];
+    }
+}
+
+template <int UNUSED = 0>
+__global__ void k_reduce_final(const double* part, int nblocks, double* out) {
+    // one warp, fixed order: lane-strided partial sums, then a shuffle tree
+    double s1 = 0.0, s2 = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += 32) {
+        s1 += part[2 * b];
+        s2 += part[2 * b + 1];
+    }
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if (threadIdx.x == 0) {
+        out[0] = s1;
+        out[1] = s2;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side of the engine.
+// ---------------------------------------------------------------------------
+#define LB_CUDA(call)                                                                     \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            err = std::string(#call) + ": " + cudaGetErrorString(e_);                     \
+            return 2;                                                                     \
+        }                                                                                 \
+    } while (0)
+
+template <typename T, class LF, class LG>
+class Engine final : public ISim {
+   public:
+    ~Engine() override { release(); }
+
+    int init(const lbrbc_params& P, const uint8_t* mask, const lbrbc_init* ini, std::string& err) override {
+        (void)cudaGetLastError();  // do not report an error left by earlier, unrelated calls
+        prm_ = P;
+        Geo& g = d_.geo;
+        g.nx = P.nx;
+        g.ny = P.ny;
+        g.nz = P.dim == 2 ? 1 : P.nz;
+        g.per_x = P.bc[0] == LBRBC_PERIODIC;
+        g.per_y = P.bc[1] == LBRBC_PERIODIC;
+        g.per_z = P.dim == 2 ? 1 : P.bc[2] == LBRBC_PERIODIC;
+        g.open_x = P.bc[0] == LBRBC_OPEN;
+        g.py = g.per_y ? 0 : 1;
+        g.pz = g.per_z ? 0 : 1;
+        g.SX = ((g.nx + 2 + 31) / 32) * 32;
+        g.SY = g.ny + 2 * g.py;
+        g.SZ = g.nz + 2 * g.pz;
+        g.OFF = 32;
+        g.NP = ((g.OFF + (long long)g.SX * g.SY * g.SZ + 64 + 63) / 64) * 64;
+        ncell_ = (long long)g.nx * g.ny * g.nz;
+        if (g.NP >= (1LL << 31)) {
+            err = "grid too large for 32-bit cell indices";
+            return 1;
+        }
+        // physics
+        Phys& p = ph_;
+        const bool trt_f = P.magic_flow >= 0.0, trt_g = P.magic_solute >= 0.0;
+        p.trt_f = trt_f;
+        p.trt_g = trt_g;
+        p.of_sym = 1.0 / P.tau_flow;
+        p.of_anti = trt_f ? 1.0 / (0.5 + P.magic_flow / (P.tau_flow - 0.5)) : p.of_sym;
+        p.og_anti = 1.0 / P.tau_solute;
+        p.og_sym = trt_g ? 1.0 / (0.5 + P.magic_solute / (P.tau_solute - 0.5)) : p.og_anti;
+        if (LG::Q == 9) {
+            p.gcs2 = 1.0 / 3.0;
+            p.gw0 = 4.0 / 9.0;
+            p.gw1 = 1.0 / 9.0;
+        } else {
+            double J0 = P.rest_fraction;
+            if (J0 < 0.0) J0 = (LG::DIM == 2) ? 1.0 / 3.0 : 0.25;
+            p.gcs2 = (1.0 - J0) / LG::DIM;
+            p.gw0 = J0;
+            p.gw1 = p.gcs2 / 2.0;
+            if (P.rest_fraction < 0.0 && LG::DIM == 2) {
+                p.gw0 = 1.0 / 3.0;
+                p.gw1 = 1.0 / 6.0;
+                p.gcs2 = 1.0 / 3.0;
+            }
+        }
+        p.cref = P.c_init != 0.0 ? P.c_init : (P.c_eq != 0.0 ? P.c_eq : P.c_dirichlet);
+        p.c_inlet = P.c_inlet;
+        p.rho_out = P.rho_outlet;
+        p.c_dir = P.c_dirichlet;
+        p.c_eq = P.c_eq;
+        p.k_r = P.k_r;
+        p.gamma = P.tau_solute / (P.tau_solute - 0.5);
+        p.Vm = P.molar_volume;
+        p.rho_init = P.rho_init;
+        p.scheme = P.scheme;
+        p.phase_change = P.phase_change;
+
+        // kinds with ghosts, host side
+        const long long NP = g.NP;
+        std::vector<uint8_t> kind(NP, KIND_OUTSIDE);
+        long long nsolid = 0, nfluid = 0;
+        for (int z = 0; z < g.nz; ++z)
+            for (int y = 0; y < g.ny; ++y)
+                for (int x = 0; x < g.nx; ++x) {
+                    const uint8_t m = mask[x + (long long)g.nx * (y + (long long)g.ny * z)];
+                    kind[g.idx(x, y, z)] = m;
+                    if (m == KIND_FLUID) nfluid++;
+                    else nsolid++;
+                }
+        nfluid_ = nfluid;
+        // list capacities: the initial counts with head room for growth
+        long long nb0 = 0, nf0 = 0;
+        count_lists_host(kind, nb0, nf0);
+        nb0_ = nb0;
+        auto grow = [&](long long n0) {
+            long long c = std::max<long long>(4 * n0, n0 + ncell_ / 16) + 1024;
+            return (int)std::min<long long>(c, ncell_ + 1024);
+        };
+        d_.cap_b = grow(nb0);
+        d_.cap_f = grow(nf0);
+        d_.cap_e = (int)std::min<long long>(ncell_ + 64, std::max<long long>(1 << 16, ncell_ / 64));
+        d_.cap_log = P.event_log_capacity > 0 ? P.event_log_capacity : 0;
+        nchunks_ = (int)((ncell_ + SCAN_CHUNK - 1) / SCAN_CHUNK);
+
+        // device allocations
+        constexpr int QF = LF::Q > 0 ? LF::Q : 0, QG = LG::Q;
+        if (QF) LB_CUDA(dalloc(&d_.F, (size_t)QF * NP));
+        else d_.F = nullptr;
+        LB_CUDA(dalloc(&d_.G, (size_t)QG * NP));
+        LB_CUDA(dalloc(&d_.nw, (size_t)NP));
+        LB_CUDA(dalloc(&d_.kind, (size_t)NP));
+        LB_CUDA(dalloc(&d_.phi, (size_t)NP));
+        LB_CUDA(dalloc(&d_.inlet_ux, (size_t)g.ny * g.nz));
+        LB_CUDA(dalloc(&d_.side, (size_t)4 * g.ny * g.nz));
+        LB_CUDA(dalloc(&d_.nb, 1));
+        LB_CUDA(dalloc(&d_.b_idx, (size_t)d_.cap_b));
+        LB_CUDA(dalloc(&d_.b_word, (size_t)d_.cap_b));
+        LB_CUDA(dalloc(&d_.b_nbr, (size_t)(QG - 1) * d_.cap_b));
+        LB_CUDA(dalloc(&d_.b_kappa, (size_t)(QG - 1) * d_.cap_b));
+        LB_CUDA(dalloc(&d_.b_share, (size_t)(QG - 1) * d_.cap_b));
+        LB_CUDA(dalloc(&d_.bmap, (size_t)NP));
+        LB_CUDA(dalloc(&d_.nf, 1));
+        LB_CUDA(dalloc(&d_.f_idx, (size_t)d_.cap_f));
+        LB_CUDA(dalloc(&d_.f_src, (size_t)(QG - 1) * d_.cap_f));
+        LB_CUDA(dalloc(&d_.nev, 1));
+        LB_CUDA(dalloc(&d_.ev_node, (size_t)d_.cap_e));
+        LB_CUDA(dalloc(&d_.ev_kind, (size_t)d_.cap_e));
+        LB_CUDA(dalloc(&d_.ev_val, (size_t)3 * d_.cap_e));
+        LB_CUDA(dalloc(&d_.ev_w, (size_t)(QG - 1) * d_.cap_e));
+        LB_CUDA(dalloc(&d_.evidx, (size_t)NP));
+        LB_CUDA(dalloc(&d_.nlog, 1));
+        if (d_.cap_log) {
+            LB_CUDA(dalloc(&d_.log_step, (size_t)d_.cap_log));
+            LB_CUDA(dalloc(&d_.log_node, (size_t)d_.cap_log));
+            LB_CUDA(dalloc(&d_.log_kind, (size_t)d_.cap_log));
+        } else {
+            d_.log_step = d_.log_node = nullptr;
+            d_.log_kind = nullptr;
+        }
+        LB_CUDA(dalloc(&d_.step, 1));
+        LB_CUDA(dalloc(&d_.acc, 4));
+        LB_CUDA(dalloc(&d_.err, 1));
+        LB_CUDA(dalloc(&d_.blk, (size_t)nchunks_ + 1));
+        LB_CUDA(cudaStreamCreateWithFlags(&own_, cudaStreamNonBlocking));
+
+        // uploads
+        std::vector<double> phi(NP, 0.0);
+        std::vector<double> c0((size_t)ncell_);
+        for (int z = 0; z < g.nz; ++z)
+            for (int y = 0; y < g.ny; ++y)
+                for (int x = 0; x < g.nx; ++x) {
+                    const long long t = x + (long long)g.nx * (y + (long long)g.ny * z);
+                    const uint8_t m = mask[t];
+                    phi[g.idx(x, y, z)] = (ini && ini->phi_init) ? ini->phi_init[t] : (m == KIND_REACTIVE ? 1.0 : 0.0);
+                    c0[t] = (ini && ini->c_init) ? ini->c_init[t] : (m == KIND_DIRICHLET ? P.c_dirichlet : P.c_init);
+                }
+        LB_CUDA(cudaMemcpy(d_.kind, kind.data(), NP, cudaMemcpyHostToDevice));
+        LB_CUDA(cudaMemcpy(d_.phi, phi.data(), NP * sizeof(double), cudaMemcpyHostToDevice));
+        if (ini && ini->k_field) {
+            std::vector<double> kf(NP, 0.0);
+            for (int z = 0; z < g.nz; ++z)
+                for (int y = 0; y < g.ny; ++y)
+                    for (int x = 0; x < g.nx; ++x)
+                        kf[g.idx(x, y, z)] = ini->k_field[x + (long long)g.nx * (y + (long long)g.ny * z)];
+            LB_CUDA(dalloc(&d_.kfield, (size_t)NP));
+            LB_CUDA(dalloc(&d_.b_krate, (size_t)d_.cap_b));
+            LB_CUDA(cudaMemcpy(d_.kfield, kf.data(), NP * sizeof(double), cudaMemcpyHostToDevice));
+        } else {
+            d_.kfield = nullptr;
+            d_.b_krate = nullptr;
+        }
+        {
+            std::vector<double> inl((size_t)g.ny * g.nz);
+            for (size_t i = 0; i < inl.size(); ++i) inl[i] = (ini && ini->inlet_ux) ? ini->inlet_ux[i] : P.u_inlet;
+            LB_CUDA(cudaMemcpy(d_.inlet_ux, inl.data(), inl.size() * sizeof(double), cudaMemcpyHostToDevice));
+        }
+        LB_CUDA(cudaMemset(d_.nw, 0, NP * sizeof(uint32_t)));
+        LB_CUDA(cudaMemset(d_.evidx, 0xff, NP * sizeof(int)));
+        LB_CUDA(cudaMemset(d_.bmap, 0xff, NP * sizeof(int)));
+        LB_CUDA(cudaMemset(d_.nev, 0, sizeof(int)));
+        LB_CUDA(cudaMemset(d_.nb, 0, sizeof(int)));
+        LB_CUDA(cudaMemset(d_.nf, 0, sizeof(int)));
+        LB_CUDA(cudaMemset(d_.nlog, 0, sizeof(long long)));
+        LB_CUDA(cudaMemset(d_.step, 0, sizeof(long long)));
+        LB_CUDA(cudaMemset(d_.acc, 0, 4 * sizeof(double)));
+        LB_CUDA(cudaMemset(d_.err, 0, sizeof(int)));
+        LB_CUDA(cudaMemset(d_.side, 0, 4 * sizeof(double) * g.ny * g.nz));
+        if (QF) LB_CUDA(cudaMemset(d_.F, 0, (size_t)QF * NP * sizeof(T)));
+        LB_CUDA(cudaMemset(d_.G, 0, (size_t)QG * NP * sizeof(T)));
+        // ghost cells are solid for every lattice
+        {
+            std::vector<uint32_t> nwh(NP, CLS_SOLID);
+            LB_CUDA(cudaMemcpy(d_.nw, nwh.data(), NP * sizeof(uint32_t), cudaMemcpyHostToDevice));
+        }
+        // classes, lists, initial populations
+        if (rebuild(own_, 0, 1, err)) return 2;
+        double *dc0 = nullptr, *du0 = nullptr;
+        LB_CUDA(talloc(&dc0, (size_t)ncell_));
+        LB_CUDA(cudaMemcpy(dc0, c0.data(), ncell_ * sizeof(double), cudaMemcpyHostToDevice));
+        if (ini && ini->u_init) {
+            LB_CUDA(talloc(&du0, (size_t)3 * ncell_));
+            LB_CUDA(cudaMemcpy(du0, ini->u_init, 3 * ncell_ * sizeof(double), cudaMemcpyHostToDevice));
+        }
+        k_init<T, LF, LG><<<grid_for(ncell_, 256), 256, 0, own_>>>(d_, ph_, dc0, du0);
+        LB_CUDA(cudaGetLastError());
+        LB_CUDA(cudaStreamSynchronize(own_));
+        cudaFree(dc0);
+        if (du0) cudaFree(du0);
+        int hnb = 0, hnf = 0, herr = 0;
+        LB_CUDA(cudaMemcpy(&hnb, d_.nb, sizeof(int), cudaMemcpyDeviceToHost));
+        LB_CUDA(cudaMemcpy(&hnf, d_.nf, sizeof(int), cudaMemcpyDeviceToHost));
+        LB_CUDA(cudaMemcpy(&herr, d_.err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (herr & ERR_OVERFLOW) {
+            err = "internal list capacity exceeded at creation";
+            return 5;
+        }
+        if (hnb != nb0) {
+            err = "device boundary list disagrees with the host count";
+            return 5;
+        }
+        lastodd_ = 1;
+        steps_ = 0;
+        if (build_graphs(err)) return 2;
+        return 0;
+    }
+
+    int step(int64_t n, cudaStream_t s, std::string& err) override {
+        cudaStream_t st = s ? s : own_;
+        int64_t k = 0;
+        // the state's parity decides which graph comes first
+        while (k < n) {
+            if (!lastodd_ || n - k < 2) {
+                // single step of the pending parity
+                LB_CUDA(cudaGraphLaunch(lastodd_ ? g_even_ : g_odd_, st));
+                lastodd_ ^= 1;
+                k += 1;
+            } else {
+                LB_CUDA(cudaGraphLaunch(g_pair_, st));
+                k += 2;
+            }
+        }
+        steps_ += n;
+        last_stream_ = st;
+        if (!s) LB_CUDA(cudaStreamSynchronize(own_));
+        return 0;
+    }
+
+    int fields(double* u, double* rho, double* c, double* phi, int device, std::string& err) override {
+        LB_CUDA(cudaStreamSynchronize(last_stream_ ? last_stream_ : own_));
+        double *du = u, *dr = rho, *dc = c, *dp = phi;
+        double* tmp = nullptr;
+        if (!device) {
+            int nf = (u ? 3 : 0) + (rho ? 1 : 0) + (c ? 1 : 0) + (phi ? 1 : 0);
+            if (nf == 0) return 0;
+            LB_CUDA(talloc(&tmp, (size_t)nf * ncell_));
+            double* q = tmp;
+            du = u ? q : nullptr;
+            q += u ? 3 * ncell_ : 0;
+            dr = rho ? q : nullptr;
+            q += rho ? ncell_ : 0;
+            dc = c ? q : nullptr;
+            q += c ? ncell_ : 0;
+            dp = phi ? q : nullptr;
+        }
+        k_fields<T, LF, LG><<<grid_for(ncell_, 256), 256, 0, own_>>>(d_, ph_, lastodd_, du, dr, dc, dp);
+        LB_CUDA(cudaGetLastError());
+        LB_CUDA(cudaStreamSynchronize(own_));
+        if (!device) {
+            if (u) LB_CUDA(cudaMemcpy(u, du, 3 * ncell_ * sizeof(double), cudaMemcpyDeviceToHost));
+            if (rho) LB_CUDA(cudaMemcpy(rho, dr, ncell_ * sizeof(double), cudaMemcpyDeviceToHost));
+            if (c) LB_CUDA(cudaMemcpy(c, dc, ncell_ * sizeof(double), cudaMemcpyDeviceToHost));
+            if (phi) LB_CUDA(cudaMemcpy(phi, dp, ncell_ * sizeof(double), cudaMemcpyDeviceToHost));
+            cudaFree(tmp);
+        }
+        return 0;
+    }
+
+    int classes(uint8_t* out, std::string& err) override {
+        LB_CUDA(cudaStreamSynchronize(last_stream_ ? last_stream_ : own_));
+        uint8_t* tmp = nullptr;
+        LB_CUDA(talloc(&tmp, (size_t)ncell_));
+        k_classes<T><<<grid_for(ncell_, 256), 256, 0, own_>>>(d_, tmp);
+        LB_CUDA(cudaGetLastError());
+        LB_CUDA(cudaMemcpyAsync(out, tmp, ncell_, cudaMemcpyDeviceToHost, own_));
+        LB_CUDA(cudaStreamSynchronize(own_));
+        cudaFree(tmp);
+        return 0;
+    }
+
+    int ledger(double* out, std::string& err) override {
+        LB_CUDA(cudaStreamSynchronize(last_stream_ ? last_stream_ : own_));
+        const int nblk = red_blocks();
+        double* part = nullptr;
+        LB_CUDA(talloc(&part, (size_t)2 * nblk + 2));
+        k_reduce_partial<T, LG><<<nblk, RED_BLOCK, 0, own_>>>(d_, ph_, lastodd_, part);
+        k_reduce_final<0><<<1, 32, 0, own_>>>(part, nblk, part + 2 * nblk);
+        LB_CUDA(cudaGetLastError());
+        double sums[2], acc[4];
+        LB_CUDA(cudaMemcpyAsync(sums, part + 2 * nblk, 2 * sizeof(double), cudaMemcpyDeviceToHost, own_));
+        LB_CUDA(cudaMemcpyAsync(acc, d_.acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, own_));
+        LB_CUDA(cudaStreamSynchronize(own_));
+        cudaFree(part);
+        out[0] = sums[0];
+        out[1] = prm_.molar_volume > 0.0 ? sums[1] / prm_.molar_volume : 0.0;
+        out[2] = acc[2];
+        out[3] = acc[1];
+        out[4] = acc[0];
+        out[5] = (double)steps_;
+        return 0;
+    }
+
+    // Same reduction on caller-provided scratch (2 * red_blocks() + 2 doubles).
+    int ledger_with_scratch(double* out, double* part, std::string& err) {
+        LB_CUDA(cudaStreamSynchronize(last_stream_ ? last_stream_ : own_));
+        const int nblk = red_blocks();
+        k_reduce_partial<T, LG><<<nblk, RED_BLOCK, 0, own_>>>(d_, ph_, lastodd_, part);
+        k_reduce_final<0><<<1, 32, 0, own_>>>(part, nblk, part + 2 * nblk);
+        LB_CUDA(cudaGetLastError());
+        double sums[2], acc[4];
+        LB_CUDA(cudaMemcpyAsync(sums, part + 2 * nblk, 2 * sizeof(double), cudaMemcpyDeviceToHost, own_));
+        LB_CUDA(cudaMemcpyAsync(acc, d_.acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, own_));
+        LB_CUDA(cudaStreamSynchronize(own_));
+        out[0] = sums[0];
+        out[1] = prm_.molar_volume > 0.0 ? sums[1] / prm_.molar_volume : 0.0;
+        out[2] = acc[2];
+        out[3] = acc[1];
+        out[4] = acc[0];
+        out[5] = (double)steps_;
+        return 0;
+    }
+
+    int events(int64_t* count, int64_t capacity, int64_t* stp, int64_t* node, int32_t* kind, std::string& err) override {
+        LB_CUDA(cudaStreamSynchronize(last_stream_ ? last_stream_ : own_));
+        long long n = 0;
+        LB_CUDA(cudaMemcpy(&n, d_.nlog, sizeof(long long), cudaMemcpyDeviceToHost));
+        n = std::min<long long>(n, d_.cap_log);
+        *count = n;
+        const long long m = std::min<long long>(n, capacity);
+        if (m > 0 && stp) LB_CUDA(cudaMemcpy(stp, d_.log_step, m * sizeof(long long), cudaMemcpyDeviceToHost));
+        if (m > 0 && node) LB_CUDA(cudaMemcpy(node, d_.log_node, m * sizeof(long long), cudaMemcpyDeviceToHost));
+        if (m > 0 && kind) LB_CUDA(cudaMemcpy(kind, d_.log_kind, m * sizeof(int), cudaMemcpyDeviceToHost));
+        return 0;
+    }
+
+    int check(std::string& err) override {
+        LB_CUDA(cudaStreamSynchronize(last_stream_ ? last_stream_ : own_));
+        LB_CUDA(cudaDeviceSynchronize());
+        int herr = 0;
+        LB_CUDA(cudaMemcpy(&herr, d_.err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (herr & ERR_OVERFLOW) {
+            err = "an internal list (events / boundary cells) exceeded its capacity";
+            return 5;
+        }
+        if (herr & ERR_NUMERIC) {
+            err = "non-finite concentration or non-positive density encountered";
+            return 3;
+        }
+        return 0;
+    }
+
+    long long fluid_cells() const override { return nfluid_; }
+    long long boundary_cells() const override { return nb0_; }
+    int red_blocks() const { return (int)std::min<long long>(1024, (ncell_ + RED_BLOCK - 1) / RED_BLOCK); }
+    const Dev<T>& dev() const { return d_; }
+    const Phys& phys() const { return ph_; }
+    int last_odd() const { return lastodd_; }
+    cudaStream_t own_stream() const { return own_; }
+    cudaStream_t last_stream() const { return last_stream_; }
+
+   private:
+    // Allocation owned by the simulation until release().
+    template <typename U>
+    cudaError_t dalloc(U** p, size_t n) {
+        cudaError_t e = cudaMalloc((void**)p, n * sizeof(U) + 16);
+        if (e == cudaSuccess) allocs_.push_back((void*)*p);
+        return e;
+    }
+    // Temporary allocation, freed by the caller.
+    template <typename U>
+    static cudaError_t talloc(U** p, size_t n) {
+        return cudaMalloc((void**)p, n * sizeof(U) + 16);
+    }
+
+    static int grid_for(long long n, int block) {
+        long long b = (n + block - 1) / block;
+        return (int)std::max<long long>(1, std::min<long long>(b, 152LL * 16));
+    }
+
+    void count_lists_host(const std::vector<uint8_t>& kind, long long& nb, long long& nf) const {
+        const Geo& g = d_.geo;
+        auto inside = [&](int& x, int& y, int& z) {
+            if (x < 0 || x >= g.nx) {
+                if (!g.per_x) return false;
+                x = (x + g.nx) % g.nx;
+            }
+            if (y < 0 || y >= g.ny) {
+                if (!g.per_y) return false;
+                y = (y + g.ny) % g.ny;
+            }
+            if (z < 0 || z >= g.nz) {
+                if (!g.per_z) return false;
+                z = (z + g.nz) % g.nz;
+            }
+            return true;
+        };
+        auto cls = [&](int x, int y, int z) -> int {
+            if (!inside(x, y, z)) return CLS_SOLID;
+            if (kind[g.idx(x, y, z)] == KIND_FLUID) return CLS_FLUID;
+            for (int o = 1; o < LG::Q; ++o) {
+                int xx = x + LG::cx(o), yy = y + LG::cy(o), zz = z + LG::cz(o);
+                if (inside(xx, yy, zz) && kind[g.idx(xx, yy, zz)] == KIND_FLUID) return CLS_BOUND;
+            }
+            return CLS_SOLID;
+        };
+        nb = nf = 0;
+        for (int z = 0; z < g.nz; ++z)
+            for (int y = 0; y < g.ny; ++y)
+                for (int x = 0; x < g.nx; ++x) {
+                    const int c = cls(x, y, z);
+                    if (c == CLS_BOUND) nb++;
+                    if (c == CLS_FLUID) {
+                        for (int o = 1; o < LG::Q; ++o) {
+                            int xx = x - LG::cx(o), yy = y - LG::cy(o), zz = z - LG::cz(o);
+                            if (!inside(xx, yy, zz)) continue;
+                            if (kind[g.idx(xx, yy, zz)] == KIND_REACTIVE) {
+                                nf++;
+                                break;
+                            }
+                        }
+                    }
+                }
+    }
+
+    // Reclassification and list rebuild (force = 1 at creation: unconditional).
+    int rebuild(cudaStream_t st, int lastodd, int force, std::string& err) {
+        k_reclassify<T, LF, LG><<<grid_for(ncell_, 256), 256, 0, st>>>(d_, ph_, lastodd, force);
+        for (int which = 0; which < 2; ++which) {
+            k_count<T, LG><<<nchunks_, 256, 0, st>>>(d_, which, force);
+            k_scan<T><<<1, 1024, 0, st>>>(d_, nchunks_, which, force);
+            k_write_lists<T, LG><<<nchunks_, 256, 0, st>>>(d_, ph_, which, force);
+        }
+        LB_CUDA(cudaGetLastError());
+        return 0;
+    }
+
+    // One time step; with `ev` (5 events) the kernel groups are bracketed by
+    // event records: fluid sweep, boundary list, fluid ends, phase change.
+    int enqueue_step(cudaStream_t st, bool odd, std::string& err, cudaEvent_t* ev = nullptr) {
+        const Geo& g = d_.geo;
+        dim3 grid((g.nx + FLUID_BLOCK - 1) / FLUID_BLOCK, g.ny, g.nz);
+        if (ev) LB_CUDA(cudaEventRecord(ev[0], st));
+        if (odd) k_fluid<T, LF, LG, true><<<grid, FLUID_BLOCK, 0, st>>>(d_, ph_);
+        else k_fluid<T, LF, LG, false><<<grid, FLUID_BLOCK, 0, st>>>(d_, ph_);
+        if (ev) LB_CUDA(cudaEventRecord(ev[1], st));
+        const int lg = list_grid(d_.cap_b);
+        if (odd) k_bound<T, LG, true><<<lg, LIST_BLOCK, 0, st>>>(d_, ph_);
+        else k_bound<T, LG, false><<<lg, LIST_BLOCK, 0, st>>>(d_, ph_);
+        if (ev) LB_CUDA(cudaEventRecord(ev[2], st));
+        k_fend<T, LG><<<list_grid(d_.cap_f), LIST_BLOCK, 0, st>>>(d_, ph_);
+        if (ev) LB_CUDA(cudaEventRecord(ev[3], st));
+        if (ph_.phase_change) {
+            const int eg = 152 * 2;
+            const int lo = odd ? 1 : 0;
+            k_ev_mark<T><<<eg, 256, 0, st>>>(d_);
+            k_ev_compute<T, LF, LG><<<eg, 256, 0, st>>>(d_, ph_, lo);
+            k_ev_apply_self<T, LF, LG><<<eg, 256, 0, st>>>(d_, ph_, lo);
+            k_ev_neighbours<T, LG><<<eg, 256, 0, st>>>(d_, ph_, lo);
+            if (rebuild(st, lo, 0, err)) return 2;
+            k_ev_reset<T><<<eg, 256, 0, st>>>(d_);
+            k_step_end<T><<<1, 1, 0, st>>>(d_);
+        }
+        if (ev) LB_CUDA(cudaEventRecord(ev[4], st));
+        LB_CUDA(cudaGetLastError());
+        return 0;
+    }
+
+   public:
+    // Number of kernel launches of one step.
+    int launches_per_step() const override { return 3 + (ph_.phase_change ? 5 + 3 * 2 + 2 + 1 : 0); }
+
+    // Run n steps without graphs, timing each kernel group with CUDA events on
+    // the stream the kernels run on; ms[g] = mean duration of group g.
+    int profile(int64_t n, cudaStream_t s, double* ms, std::string& err) override {
+        cudaStream_t st = s ? s : own_;
+        n = std::max<int64_t>(1, std::min<int64_t>(n, 4096));
+        std::vector<cudaEvent_t> ev((size_t)5 * n);
+        for (auto& e : ev) LB_CUDA(cudaEventCreate(&e));
+        for (int64_t k = 0; k < n; ++k) {
+            const bool odd = !lastodd_;
+            if (enqueue_step(st, odd, err, &ev[(size_t)5 * k])) return 2;
+            lastodd_ ^= 1;
+        }
+        steps_ += n;
+        last_stream_ = st;
+        LB_CUDA(cudaStreamSynchronize(st));
+        double acc[4] = {0, 0, 0, 0};
+        for (int64_t k = 0; k < n; ++k)
+            for (int q = 0; q < 4; ++q) {
+                float t = 0.f;
+                LB_CUDA(cudaEventElapsedTime(&t, ev[(size_t)5 * k + q], ev[(size_t)5 * k + q + 1]));
+                acc[q] += t;
+            }
+        for (int q = 0; q < 4; ++q) ms[q] = acc[q] / (double)n;
+        for (auto& e : ev) cudaEventDestroy(e);
+        return 0;
+    }
+
+   private:
+    static int list_grid(int cap) {
+        return (int)std::max(1, std::min(152 * 8, (cap + LIST_BLOCK - 1) / LIST_BLOCK));
+    }
+
+    int build_graphs(std::string& err) {
+        cudaStream_t cs;
+        LB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        auto cap = [&](cudaGraphExec_t* out, int mode) -> int {
+            cudaGraph_t gr;
+            LB_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            int r = 0;
+            if (mode == 0) r = enqueue_step(cs, false, err);
+            else if (mode == 1) r = enqueue_step(cs, true, err);
+            else {
+                r = enqueue_step(cs, false, err);
+                if (!r) r = enqueue_step(cs, true, err);
+            }
+            cudaError_t e = cudaStreamEndCapture(cs, &gr);
+            if (r) return r;
+            if (e != cudaSuccess) {
+                err = std::string("graph capture: ") + cudaGetErrorString(e);
+                return 2;
+            }
+            LB_CUDA(cudaGraphInstantiate(out, gr, 0));
+            cudaGraphDestroy(gr);
+            return 0;
+        };
+        if (cap(&g_even_, 0) || cap(&g_odd_, 1) || cap(&g_pair_, 2)) {
+            cudaStreamDestroy(cs);
+            return 2;
+        }
+        graphs_ = true;
+        cudaStreamDestroy(cs);
+        return 0;
+    }
+
+    void release() {
+        if (graphs_) {
+            cudaGraphExecDestroy(g_even_);
+            cudaGraphExecDestroy(g_odd_);
+            cudaGraphExecDestroy(g_pair_);
+            graphs_ = false;
+        }
+        if (own_) cudaStreamSynchronize(own_);
+        for (void* p : allocs_) cudaFree(p);
+        allocs_.clear();
+        if (own_) cudaStreamDestroy(own_);
+        own_ = nullptr;
+    }
+
+    lbrbc_params prm_{};
+    Dev<T> d_{};
+    Phys ph_{};
+    long long ncell_ = 0, nfluid_ = 0, nb0_ = 0;
+    int nchunks_ = 0;
+    int lastodd_ = 1;
+    int64_t steps_ = 0;
+    cudaStream_t own_ = nullptr, last_stream_ = nullptr;
+    cudaGraphExec_t g_even_{}, g_odd_{}, g_pair_{};
+    bool graphs_ = false;
+    std::vector<void*> allocs_;
+};
+
+#undef LB_CUDA
+
+}  // namespace lbrbc

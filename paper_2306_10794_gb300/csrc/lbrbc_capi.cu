@@ -1,0 +1,172 @@
+// C ABI of the library: argument validation, dispatch to the engines, error
+// messages.  The declarations and their documentation are in include/lbrbc.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "sim_iface.h"
+
+struct lbrbc_sim {
+    lbrbc::ISim* impl = nullptr;
+    std::string err;
+    int device = 0;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+lbrbc_status fail(lbrbc_sim* s, int code, const std::string& msg) {
+    if (s) s->err = msg;
+    else g_create_error = msg;
+    return (lbrbc_status)code;
+}
+
+std::string validate(const lbrbc_params& p) {
+    if (p.dim != 2 && p.dim != 3) return "dim must be 2 or 3";
+    if (p.nx < 1 || p.ny < 1 || (p.dim == 3 && p.nz < 1)) return "grid sizes must be positive";
+    if (p.dim == 2 && p.nz != 1 && p.nz != 0) return "2D grids need nz = 1";
+    if (p.dim == 3 && !((p.flow_q == 19 || p.flow_q == 0) && p.solute_q == 7))
+        return "3D needs flow_q in {19, 0} and solute_q = 7";
+    if (p.dim == 2 && !((p.flow_q == 9 && p.solute_q == 5) || (p.flow_q == 0 && (p.solute_q == 5 || p.solute_q == 9))))
+        return "2D needs (flow_q, solute_q) in {(9, 5), (0, 5), (0, 9)}";
+    for (int a = 0; a < 3; ++a) {
+        if (p.bc[a] < LBRBC_PERIODIC || p.bc[a] > LBRBC_OPEN) return "bc must be PERIODIC, WALL or OPEN";
+        if (a > 0 && p.bc[a] == LBRBC_OPEN) return "only the x axis may be OPEN";
+    }
+    if (p.bc[0] == LBRBC_OPEN && p.nx < 2) return "an OPEN x axis needs nx >= 2";
+    if (!(p.tau_solute > 0.5)) return "tau_solute must exceed 1/2";
+    if (p.flow_q && !(p.tau_flow > 0.5)) return "tau_flow must exceed 1/2";
+    if (p.magic_flow == 0.0 || p.magic_solute == 0.0) return "Lambda = 0 is singular (use < 0 for BGK)";
+    if (p.rest_fraction >= 1.0) return "rest_fraction must be < 1";
+    if (p.rest_fraction >= 0.0 && p.solute_q == 9) return "the rest fraction applies to D2Q5 / D3Q7 only";
+    if (!(p.k_r >= 0.0) || !(p.c_eq >= 0.0)) return "k_r and c_eq must be >= 0";
+    if (!(p.molar_volume >= 0.0)) return "molar_volume must be >= 0";
+    if (p.phase_change && !(p.molar_volume > 0.0)) return "phase change needs molar_volume > 0";
+    if (p.scheme < LBRBC_SCHEME_NEW || p.scheme > LBRBC_SCHEME_ANTI_BB) return "unknown scheme";
+    if (p.precision != LBRBC_FP32 && p.precision != LBRBC_FP64) return "precision must be FP32 or FP64";
+    if (!(p.rho_init > 0.0)) return "rho_init must be positive";
+    if (p.event_log_capacity < 0) return "event_log_capacity must be >= 0";
+    return "";
+}
+
+}  // namespace
+
+extern "C" {
+
+lbrbc_status lbrbc_create(const lbrbc_params* params, const uint8_t* mask, const lbrbc_init* init, lbrbc_sim** out) {
+    if (!params || !mask || !out) return fail(nullptr, LBRBC_ERR_ARG, "params, mask and out must be non-NULL");
+    *out = nullptr;
+    lbrbc_params p = *params;
+    if (p.dim == 2) p.nz = 1;
+    std::string why = validate(p);
+    if (!why.empty()) return fail(nullptr, LBRBC_ERR_ARG, why);
+    const long long n = (long long)p.nx * p.ny * p.nz;
+    for (long long i = 0; i < n; ++i)
+        if (mask[i] > LBRBC_CELL_DIRICHLET) return fail(nullptr, LBRBC_ERR_ARG, "mask values must be 0, 1 or 2");
+    if (init && init->phi_init && p.phase_change)
+        for (long long i = 0; i < n; ++i)
+            if (mask[i] == LBRBC_CELL_FLUID && init->phi_init[i] >= 1.0)
+                return fail(nullptr, LBRBC_ERR_ARG, "fluid cells must start with phi < 1");
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0)
+        return fail(nullptr, LBRBC_ERR_CUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(e));
+    lbrbc::ISim* impl = p.dim == 3 ? lbrbc::make_sim_3d(p.precision, p.flow_q, p.solute_q)
+                                   : lbrbc::make_sim_2d(p.precision, p.flow_q, p.solute_q);
+    if (!impl) return fail(nullptr, LBRBC_ERR_UNSUPPORTED, "lattice combination not built");
+    lbrbc_sim* s = new (std::nothrow) lbrbc_sim();
+    if (!s) {
+        delete impl;
+        return fail(nullptr, LBRBC_ERR_ARG, "out of host memory");
+    }
+    s->impl = impl;
+    cudaGetDevice(&s->device);
+    std::string err;
+    int rc = impl->init(p, mask, init, err);
+    if (rc) {
+        delete s->impl;
+        delete s;
+        return fail(nullptr, rc, err);
+    }
+    *out = s;
+    return LBRBC_OK;
+}
+
+lbrbc_status lbrbc_step(lbrbc_sim* sim, int64_t n, void* stream) {
+    if (!sim) return fail(nullptr, LBRBC_ERR_ARG, "NULL simulation");
+    if (n < 0) return fail(sim, LBRBC_ERR_ARG, "n must be >= 0");
+    std::string err;
+    int rc = sim->impl->step(n, (cudaStream_t)stream, err);
+    return rc ? fail(sim, rc, err) : LBRBC_OK;
+}
+
+lbrbc_status lbrbc_fields(lbrbc_sim* sim, double* u, double* rho, double* c, double* phi, int device) {
+    if (!sim) return fail(nullptr, LBRBC_ERR_ARG, "NULL simulation");
+    std::string err;
+    int rc = sim->impl->fields(u, rho, c, phi, device, err);
+    return rc ? fail(sim, rc, err) : LBRBC_OK;
+}
+
+lbrbc_status lbrbc_classes(lbrbc_sim* sim, uint8_t* out) {
+    if (!sim || !out) return fail(sim, LBRBC_ERR_ARG, "NULL argument");
+    std::string err;
+    int rc = sim->impl->classes(out, err);
+    return rc ? fail(sim, rc, err) : LBRBC_OK;
+}
+
+lbrbc_status lbrbc_mass_ledger(lbrbc_sim* sim, double* out) {
+    if (!sim || !out) return fail(sim, LBRBC_ERR_ARG, "NULL argument");
+    std::string err;
+    int rc = sim->impl->ledger(out, err);
+    return rc ? fail(sim, rc, err) : LBRBC_OK;
+}
+
+lbrbc_status lbrbc_events(lbrbc_sim* sim, int64_t* count, int64_t capacity, int64_t* step, int64_t* node,
+                          int32_t* kind) {
+    if (!sim || !count) return fail(sim, LBRBC_ERR_ARG, "NULL argument");
+    if (capacity < 0) return fail(sim, LBRBC_ERR_ARG, "capacity must be >= 0");
+    std::string err;
+    int rc = sim->impl->events(count, capacity, step, node, kind, err);
+    return rc ? fail(sim, rc, err) : LBRBC_OK;
+}
+
+lbrbc_status lbrbc_profile_step(lbrbc_sim* sim, int64_t n, void* stream, double* ms_out, int64_t* launches) {
+    if (!sim || !ms_out) return fail(sim, LBRBC_ERR_ARG, "NULL argument");
+    if (n < 1) return fail(sim, LBRBC_ERR_ARG, "n must be >= 1");
+    std::string err;
+    int rc = sim->impl->profile(n, (cudaStream_t)stream, ms_out, err);
+    if (!rc && launches) *launches = sim->impl->launches_per_step();
+    return rc ? fail(sim, rc, err) : LBRBC_OK;
+}
+
+lbrbc_status lbrbc_info(lbrbc_sim* sim, int64_t* out) {
+    if (!sim || !out) return fail(sim, LBRBC_ERR_ARG, "NULL argument");
+    out[0] = sim->impl->fluid_cells();
+    out[1] = sim->impl->boundary_cells();
+    out[2] = sim->impl->launches_per_step();
+    return LBRBC_OK;
+}
+
+lbrbc_status lbrbc_check(lbrbc_sim* sim) {
+    if (!sim) return fail(nullptr, LBRBC_ERR_ARG, "NULL simulation");
+    std::string err;
+    int rc = sim->impl->check(err);
+    return rc ? fail(sim, rc, err) : LBRBC_OK;
+}
+
+const char* lbrbc_last_error(lbrbc_sim* sim) {
+    if (sim) return sim->err.c_str();
+    return g_create_error.c_str();
+}
+
+void lbrbc_destroy(lbrbc_sim* sim) {
+    if (!sim) return;
+    delete sim->impl;
+    delete sim;
+}
+
+}  // extern "C"

@@ -1,0 +1,35 @@
+// Internal interface between the C ABI and the templated device engines.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/lbrbc.h"
+
+namespace lbrbc {
+
+// Return codes follow lbrbc_status.
+class ISim {
+   public:
+    virtual ~ISim() {}
+    virtual int init(const lbrbc_params& p, const uint8_t* mask, const lbrbc_init* ini, std::string& err) = 0;
+    virtual int step(int64_t n, cudaStream_t s, std::string& err) = 0;
+    virtual int fields(double* u, double* rho, double* c, double* phi, int device, std::string& err) = 0;
+    virtual int classes(uint8_t* out, std::string& err) = 0;
+    virtual int ledger(double* out, std::string& err) = 0;
+    virtual int events(int64_t* count, int64_t capacity, int64_t* step, int64_t* node, int32_t* kind,
+                       std::string& err) = 0;
+    virtual int check(std::string& err) = 0;
+    virtual int profile(int64_t n, cudaStream_t s, double* ms, std::string& err) = 0;
+    virtual int launches_per_step() const = 0;
+    virtual long long fluid_cells() const = 0;
+    virtual long long boundary_cells() const = 0;
+};
+
+// Factories, one per translation unit; nullptr if the combination is not built.
+ISim* make_sim_3d(int precision, int flow_q, int solute_q);
+ISim* make_sim_2d(int precision, int flow_q, int solute_q);
+
+}  // namespace lbrbc

@@ -1,0 +1,288 @@
+"""Python binding of the C ABI in include/lbrbc.h (argument marshalling only).
+
+Every time step runs in the CUDA kernels of ``_lib/liblbrbc.so``; this module
+never computes any part of the method.  If the library has not been built, or
+cannot be loaded, every entry point raises: there is no CPU fallback.
+
+Functions with the C names (``lbrbc_create`` ...) take and return ctypes
+values; the ``Sim`` class wraps them for numpy / torch callers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblbrbc.so")
+
+LBRBC_OK, LBRBC_ERR_ARG, LBRBC_ERR_CUDA, LBRBC_ERR_NUMERIC = 0, 1, 2, 3
+LBRBC_ERR_TIMEOUT, LBRBC_ERR_STATE, LBRBC_ERR_UNSUPPORTED = 4, 5, 6
+BC = {"periodic": 0, "wall": 1, "open": 2}
+SCHEME = {"new": 0, "verhaeghe": 1, "patel_ju": 2, "anti_bb": 3}
+PRECISION = {"fp32": 0, "fp64": 1}
+CLASS_FLUID, CLASS_BOUND, CLASS_SOLID = 0, 1, 2
+EV_DISSOLVE, EV_PRECIPITATE = 1, 2
+
+
+class lbrbc_params(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("flow_q", ctypes.c_int), ("solute_q", ctypes.c_int), ("bc", ctypes.c_int * 3),
+        ("scheme", ctypes.c_int), ("phase_change", ctypes.c_int), ("precision", ctypes.c_int),
+        ("event_log_capacity", ctypes.c_int),
+        ("tau_flow", ctypes.c_double), ("magic_flow", ctypes.c_double), ("tau_solute", ctypes.c_double),
+        ("magic_solute", ctypes.c_double), ("rest_fraction", ctypes.c_double), ("k_r", ctypes.c_double),
+        ("c_eq", ctypes.c_double), ("molar_volume", ctypes.c_double), ("c_init", ctypes.c_double),
+        ("rho_init", ctypes.c_double), ("c_dirichlet", ctypes.c_double), ("c_inlet", ctypes.c_double),
+        ("u_inlet", ctypes.c_double), ("rho_outlet", ctypes.c_double),
+    ]
+
+
+class lbrbc_init(ctypes.Structure):
+    _fields_ = [(n, ctypes.POINTER(ctypes.c_double)) for n in
+                ("k_field", "c_init", "u_init", "phi_init", "inlet_ux")]
+
+
+class LbrbcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("lbrbc status %d: %s" % (status, msg))
+        self.status = status
+
+
+_lib = None
+
+EXPORTED = ["lbrbc_create", "lbrbc_step", "lbrbc_fields", "lbrbc_classes", "lbrbc_mass_ledger",
+            "lbrbc_events", "lbrbc_profile_step", "lbrbc_info", "lbrbc_check", "lbrbc_last_error",
+            "lbrbc_destroy"]
+
+
+def load(path: str = LIB_PATH):
+    """Load the compiled library (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("liblbrbc.so is not built (%s); run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    vp, dp = ctypes.c_void_p, P(ctypes.c_double)
+    lib.lbrbc_create.restype = ctypes.c_int
+    lib.lbrbc_create.argtypes = [P(lbrbc_params), P(ctypes.c_uint8), P(lbrbc_init), P(vp)]
+    lib.lbrbc_step.restype = ctypes.c_int
+    lib.lbrbc_step.argtypes = [vp, ctypes.c_int64, vp]
+    lib.lbrbc_fields.restype = ctypes.c_int
+    lib.lbrbc_fields.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int]
+    lib.lbrbc_classes.restype = ctypes.c_int
+    lib.lbrbc_classes.argtypes = [vp, P(ctypes.c_uint8)]
+    lib.lbrbc_mass_ledger.restype = ctypes.c_int
+    lib.lbrbc_mass_ledger.argtypes = [vp, dp]
+    lib.lbrbc_events.restype = ctypes.c_int
+    lib.lbrbc_events.argtypes = [vp, P(ctypes.c_int64), ctypes.c_int64, P(ctypes.c_int64), P(ctypes.c_int64),
+                                 P(ctypes.c_int32)]
+    lib.lbrbc_profile_step.restype = ctypes.c_int
+    lib.lbrbc_profile_step.argtypes = [vp, ctypes.c_int64, vp, dp, P(ctypes.c_int64)]
+    lib.lbrbc_info.restype = ctypes.c_int
+    lib.lbrbc_info.argtypes = [vp, P(ctypes.c_int64)]
+    lib.lbrbc_check.restype = ctypes.c_int
+    lib.lbrbc_check.argtypes = [vp]
+    lib.lbrbc_last_error.restype = ctypes.c_char_p
+    lib.lbrbc_last_error.argtypes = [vp]
+    lib.lbrbc_destroy.restype = None
+    lib.lbrbc_destroy.argtypes = [vp]
+    _lib = lib
+    return lib
+
+
+def _check(lib, handle, st):
+    if st != LBRBC_OK:
+        raise LbrbcError(st, lib.lbrbc_last_error(handle).decode())
+
+
+# Thin wrappers with the C names -------------------------------------------------
+def lbrbc_create(params: lbrbc_params, mask: np.ndarray, init: lbrbc_init | None = None):
+    lib = load()
+    h = ctypes.c_void_p()
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    st = lib.lbrbc_create(ctypes.byref(params), m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                          ctypes.byref(init) if init is not None else None, ctypes.byref(h))
+    _check(lib, None, st)
+    return h
+
+
+def lbrbc_step(handle, n: int, stream: int | None = None):
+    lib = load()
+    _check(lib, handle, lib.lbrbc_step(handle, int(n), ctypes.c_void_p(stream) if stream else None))
+
+
+def lbrbc_fields(handle, u=None, rho=None, c=None, phi=None, device: bool = False):
+    """Pointers as ints (device) or numpy float64 arrays (host)."""
+    lib = load()
+
+    def ptr(a):
+        if a is None:
+            return None
+        if isinstance(a, int):
+            return ctypes.c_void_p(a)
+        return ctypes.c_void_p(a.ctypes.data)
+
+    _check(lib, handle, lib.lbrbc_fields(handle, ptr(u), ptr(rho), ptr(c), ptr(phi), int(device)))
+
+
+def lbrbc_classes(handle, out: np.ndarray):
+    lib = load()
+    _check(lib, handle, lib.lbrbc_classes(handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
+
+
+def lbrbc_mass_ledger(handle):
+    lib = load()
+    out = np.zeros(6)
+    _check(lib, handle, lib.lbrbc_mass_ledger(handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
+
+
+def lbrbc_events(handle):
+    lib = load()
+    n = ctypes.c_int64()
+    _check(lib, handle, lib.lbrbc_events(handle, ctypes.byref(n), 0, None, None, None))
+    k = n.value
+    st, nd, kd = np.zeros(k, np.int64), np.zeros(k, np.int64), np.zeros(k, np.int32)
+    if k:
+        P = ctypes.POINTER
+        _check(lib, handle, lib.lbrbc_events(handle, ctypes.byref(n), k, st.ctypes.data_as(P(ctypes.c_int64)),
+                                             nd.ctypes.data_as(P(ctypes.c_int64)),
+                                             kd.ctypes.data_as(P(ctypes.c_int32))))
+    return st, nd, kd
+
+
+def lbrbc_profile_step(handle, n: int, stream: int | None = None):
+    """(ms per step of [fluid, boundary, fluid-end, phase-change] kernels, launches per step)."""
+    lib = load()
+    ms = np.zeros(4)
+    nl = ctypes.c_int64()
+    _check(lib, handle, lib.lbrbc_profile_step(handle, int(n), ctypes.c_void_p(stream) if stream else None,
+                                               ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(nl)))
+    return ms, nl.value
+
+
+def lbrbc_info(handle):
+    lib = load()
+    out = (ctypes.c_int64 * 3)()
+    _check(lib, handle, lib.lbrbc_info(handle, out))
+    return dict(fluid_cells=out[0], boundary_cells=out[1], launches_per_step=out[2])
+
+
+def lbrbc_check(handle):
+    lib = load()
+    _check(lib, handle, lib.lbrbc_check(handle))
+
+
+def lbrbc_last_error(handle=None) -> str:
+    return load().lbrbc_last_error(handle).decode()
+
+
+def lbrbc_destroy(handle):
+    if handle:
+        load().lbrbc_destroy(handle)
+
+
+# Convenience wrapper -------------------------------------------------------------
+DEFAULTS = dict(dim=3, nx=8, ny=8, nz=8, flow_q=19, solute_q=7, bc=("periodic", "periodic", "periodic"),
+                scheme="new", phase_change=0, precision="fp32", event_log_capacity=0, tau_flow=0.8,
+                magic_flow=-1.0, tau_solute=0.8, magic_solute=-1.0, rest_fraction=-1.0, k_r=0.0, c_eq=0.0,
+                molar_volume=1.0, c_init=0.0, rho_init=1.0, c_dirichlet=0.0, c_inlet=0.0, u_inlet=0.0,
+                rho_outlet=1.0)
+
+
+def make_params(p: dict) -> lbrbc_params:
+    q = dict(DEFAULTS)
+    q.update(p)
+    s = lbrbc_params()
+    for k in ("dim", "nx", "ny", "nz", "flow_q", "solute_q", "phase_change", "event_log_capacity"):
+        setattr(s, k, int(q[k]))
+    if q["dim"] == 2:
+        s.nz = 1
+    for a in range(3):
+        s.bc[a] = BC[q["bc"][a]] if isinstance(q["bc"][a], str) else int(q["bc"][a])
+    s.scheme = SCHEME[q["scheme"]] if isinstance(q["scheme"], str) else int(q["scheme"])
+    s.precision = PRECISION[q["precision"]] if isinstance(q["precision"], str) else int(q["precision"])
+    for k in ("tau_flow", "magic_flow", "tau_solute", "magic_solute", "rest_fraction", "k_r", "c_eq",
+              "molar_volume", "c_init", "rho_init", "c_dirichlet", "c_inlet", "u_inlet", "rho_outlet"):
+        setattr(s, k, float(q[k]))
+    return s
+
+
+class Sim:
+    """One GPU simulation.  ``mask``: uint8 [z, y, x] (0 fluid, 1 reactive
+    solid, 2 Dirichlet solid); optional init fields as numpy arrays."""
+
+    def __init__(self, params: dict, mask, k_field=None, c_init=None, u_init=None, phi_init=None,
+                 inlet_ux=None):
+        self._lib = load()
+        self._p = make_params(params)
+        self.shape = (self._p.nz, self._p.ny, self._p.nx)
+        self.N = int(np.prod(self.shape))
+        m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8).reshape(-1))
+        if m.size != self.N:
+            raise ValueError("mask size %d != grid %d" % (m.size, self.N))
+        self._keep = {}
+        ini = lbrbc_init()
+        for name, arr, n in (("k_field", k_field, self.N), ("c_init", c_init, self.N), ("u_init", u_init, 3 * self.N),
+                             ("phi_init", phi_init, self.N), ("inlet_ux", inlet_ux, self._p.ny * self._p.nz)):
+            if arr is None:
+                continue
+            a = np.ascontiguousarray(np.asarray(arr, dtype=np.float64).reshape(-1))
+            if a.size != n:
+                raise ValueError("%s has %d entries, expected %d" % (name, a.size, n))
+            self._keep[name] = a
+            setattr(ini, name, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        self._h = lbrbc_create(self._p, m, ini)
+
+    def step(self, n: int = 1, stream: int | None = None):
+        lbrbc_step(self._h, n, stream)
+
+    def fields(self):
+        u = np.zeros(3 * self.N)
+        rho, c, phi = np.zeros(self.N), np.zeros(self.N), np.zeros(self.N)
+        lbrbc_fields(self._h, u, rho, c, phi)
+        s = self.shape
+        return u.reshape(s + (3,)), rho.reshape(s), c.reshape(s), phi.reshape(s)
+
+    def fields_device(self, u=None, rho=None, c=None, phi=None):
+        """Write into device buffers given as torch tensors (float64, cuda)."""
+        ptr = lambda t: None if t is None else int(t.data_ptr())
+        lbrbc_fields(self._h, ptr(u), ptr(rho), ptr(c), ptr(phi), device=True)
+
+    def classes(self):
+        out = np.zeros(self.N, np.uint8)
+        lbrbc_classes(self._h, out)
+        return out.reshape(self.shape)
+
+    def ledger(self) -> dict:
+        o = lbrbc_mass_ledger(self._h)
+        return dict(solute=o[0], solid_over_vm=o[1], unpaid=o[2], dirichlet_in=o[3], reacted=o[4], step=int(o[5]))
+
+    def events(self):
+        st, nd, kd = lbrbc_events(self._h)
+        return np.stack([st, nd, kd.astype(np.int64)], axis=1) if len(st) else np.zeros((0, 3), np.int64)
+
+    def check(self):
+        lbrbc_check(self._h)
+
+    def profile(self, n: int, stream: int | None = None):
+        return lbrbc_profile_step(self._h, n, stream)
+
+    def info(self) -> dict:
+        return lbrbc_info(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lbrbc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -275,7 +275,11 @@ static void classify(orc_sim *s, const unsigned char *kind, unsigned char *cls)
 
 /* Wall normal by the isotropic finite-difference gradient of the solid
  * indicator (Sec. 3.2 names the method): grad s = cs^-2 sum_i w_i s(x+e_i) e_i
- * over D2Q9 / D3Q19; n = -grad s / |grad s| points from solid into fluid. */
+ * over D2Q9 / D3Q19; n = -grad s / |grad s| points from solid into fluid.
+ * The sum is evaluated exactly: with the integer weights 36 w_i it is an
+ * integer vector proportional to grad s, so components that vanish by
+ * symmetry are exactly zero (the split of the precipitation excess, Sec. 2.4,
+ * changes discontinuously when sum (e_o . n)_+ reaches zero). */
 static void compute_normals(orc_sim *s)
 {
     const orc_lat *L = &s->LN;
@@ -283,17 +287,18 @@ static void compute_normals(orc_sim *s)
         for (int y = 0; y < s->p.ny; ++y)
             for (int x = 0; x < s->p.nx; ++x) {
                 long id = IDX(s, x, y, z);
-                double g[3] = {0, 0, 0};
+                long gi[3] = {0, 0, 0};
                 s->normal_ok[id] = 0;
                 s->normal[3 * id] = s->normal[3 * id + 1] = s->normal[3 * id + 2] = 0.0;
                 if (s->cls[id] != ORC_BOUND) continue;
                 for (int i = 1; i < L->q; ++i) {
-                    double si = solid_indicator(s, s->kind, x, y, z, L->e[i]);
-                    for (int a = 0; a < 3; ++a) g[a] += L->w[i] * si * L->e[i][a] / L->cs2;
+                    long wi = lround(36.0 * L->w[i]);
+                    long si = (long)solid_indicator(s, s->kind, x, y, z, L->e[i]);
+                    for (int a = 0; a < 3; ++a) gi[a] += wi * si * L->e[i][a];
                 }
-                double len = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-                if (len < 1e-12) continue;
-                for (int a = 0; a < 3; ++a) s->normal[3 * id + a] = -g[a] / len;
+                if (gi[0] == 0 && gi[1] == 0 && gi[2] == 0) continue;
+                double len = sqrt((double)(gi[0] * gi[0] + gi[1] * gi[1] + gi[2] * gi[2]));
+                for (int a = 0; a < 3; ++a) s->normal[3 * id + a] = -(double)gi[a] / len;
                 s->normal_ok[id] = 1;
             }
 }

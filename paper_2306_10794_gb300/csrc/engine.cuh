@@ -49,7 +49,15 @@ constexpr int GBIT = 20;
 constexpr int BW_LINK = 8;
 constexpr uint32_t BW_DIRICHLET = 1u << 16;
 
-constexpr int FLUID_BLOCK = 128;
+#ifndef LBRBC_FLUID_BLOCK
+#define LBRBC_FLUID_BLOCK 128
+#endif
+// Population loads / stores of the fluid sweep: 0 default caching, 1
+// evict-first (each population is touched once per step).
+#ifndef LBRBC_STREAM_HINT
+#define LBRBC_STREAM_HINT 1
+#endif
+constexpr int FLUID_BLOCK = LBRBC_FLUID_BLOCK;
 constexpr int LIST_BLOCK = 256;
 constexpr int SCAN_CHUNK = 1024;
 
@@ -138,7 +146,7 @@ struct Dev {
     int* nb;
     int* b_idx;
     uint32_t* b_word;
-    long long* b_nbr;     // (QG-1) * cap_b
+    uint64_t* b_xyz;      // packed cell coordinates (21 bits each)
     T* b_kappa;           // (QG-1) * cap_b
     double* b_krate;      // cap_b or null
     double* b_share;      // (QG-1) * cap_b
@@ -163,7 +171,8 @@ struct Dev {
     long long* log_node;
     int* log_kind;
     long long* step;      // completed steps
-    double* acc;          // [0] reacted, [1] Dirichlet inflow, [2] unpaid
+    double* acc;          // [0] reacted, [1] Dirichlet inflow, [2] unpaid (event path)
+    double* bacc;         // per-block partial ledger of k_bound: 2 * gridDim.x
     int* err;
     // compaction scratch
     int* blk;             // per chunk counts / offsets
@@ -248,54 +257,140 @@ __device__ __forceinline__ void collide_solute(T (&g)[L::Q], T C, T ux, T uy, T 
 
 // ---------------------------------------------------------------------------
 // Fluid cells: stream (read side), boundary rules, moments, collide, write.
+// Element indices are 32-bit (checked at creation: Q * NP < 2^32), all loads
+// of both lattices are issued before any arithmetic, and cells without an
+// inactive source take a path with no per-direction tests.
 // ---------------------------------------------------------------------------
+struct Nbr32 {
+    int xp, xm, yp, ym, zp, zm;
+};
+
+__device__ __forceinline__ Nbr32 nbr32(const Geo& g, int x, int y, int z) {
+    Nbr32 d;
+    const int sy = g.SX, sz = g.SX * g.SY;
+    d.xp = (g.per_x && x == g.nx - 1) ? -(g.nx - 1) : 1;
+    d.xm = (g.per_x && x == 0) ? (g.nx - 1) : -1;
+    d.yp = (g.per_y && y == g.ny - 1) ? -(g.ny - 1) * sy : sy;
+    d.ym = (g.per_y && y == 0) ? (g.ny - 1) * sy : -sy;
+    d.zp = (g.per_z && z == g.nz - 1) ? -(g.nz - 1) * sz : sz;
+    d.zm = (g.per_z && z == 0) ? (g.nz - 1) * sz : -sz;
+    return d;
+}
+
+template <class L>
+__device__ __forceinline__ uint32_t off32(const Nbr32& d, int i) {
+    return (uint32_t)((L::cx(i) > 0 ? d.xp : (L::cx(i) < 0 ? d.xm : 0)) +
+                      (L::cy(i) > 0 ? d.yp : (L::cy(i) < 0 ? d.ym : 0)) +
+                      (L::cz(i) > 0 ? d.zp : (L::cz(i) < 0 ? d.zm : 0)));
+}
+
+// Slot read by a cell for direction i: its own slot i (even step) or the
+// slot opp(i) of the source x - e_i (odd step); an inactive source swaps
+// the two (the value there is the cell's own f*_opp(i)).
+template <class L, bool ODD>
+__device__ __forceinline__ uint32_t read_slot(uint32_t id, const Nbr32& d, uint32_t NP, int i, bool inactive) {
+    const uint32_t own = (uint32_t)i * NP + id;
+    const uint32_t nbr = (uint32_t)L::opp(i) * NP + id + off32<L>(d, L::opp(i));
+    return (ODD == inactive) ? own : nbr;
+}
+
+template <class L, bool ODD>
+__device__ __forceinline__ uint32_t write_slot(uint32_t id, const Nbr32& d, uint32_t NP, int i) {
+    return ODD ? (uint32_t)i * NP + id + off32<L>(d, i) : (uint32_t)L::opp(i) * NP + id;
+}
+
+template <typename T>
+__device__ __forceinline__ T ld_pop(const T* p) {
+#if LBRBC_STREAM_HINT
+    return __ldcs(p);
+#else
+    return *p;
+#endif
+}
+template <typename T>
+__device__ __forceinline__ void st_pop(T* p, T v) {
+#if LBRBC_STREAM_HINT
+    __stcs(p, v);
+#else
+    *p = v;
+#endif
+}
+
 template <typename T, class LF, class LG, bool ODD>
 __global__ void __launch_bounds__(FLUID_BLOCK) k_fluid(const Dev<T> a, const Phys p) {
+    constexpr int QF = LF::Q, QG = LG::Q;
     const Geo& g = a.geo;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     if (x >= g.nx) return;
-    const long long id = g.idx(x, y, z);
+    const uint32_t id = (uint32_t)g.idx(x, y, z);
     const uint32_t w = a.nw[id];
     if ((w & 3u) != CLS_FLUID) return;
-    const Nbr d = nbr_deltas(g, x, y, z);
-    const long long NP = g.NP;
+    const Nbr32 d = nbr32(g, x, y, z);
+    const uint32_t NP = (uint32_t)g.NP;
+    T* __restrict__ F = a.F;
+    T* __restrict__ G = a.G;
     const bool inlet = g.open_x && x == 0;
     const bool outlet = g.open_x && x == g.nx - 1;
-    const int face = y + g.ny * z;
-    T ux = T(0), uy = T(0), uz = T(0);
-    T rho = T(1);
-    if constexpr (LF::Q > 0) {
-        T f[LF::Q];
-        T uin = T(0), uo0 = T(0), uo1 = T(0), uo2 = T(0);
-        if (inlet) uin = T(a.inlet_ux[face]);
-        if (outlet) {
-            uo0 = T(a.side[4 * face + 0]);
-            uo1 = T(a.side[4 * face + 1]);
-            uo2 = T(a.side[4 * face + 2]);
+    const bool plain = (w >> FBIT) == 0u && !inlet && !outlet;
+
+    T f[QF > 0 ? QF : 1];
+    T gg[QG];
+    if (plain) {
+#pragma unroll
+        for (int i = 0; i < QF; ++i) f[i] = ld_pop(F + read_slot<LF, ODD>(id, d, NP, i, false));
+#pragma unroll
+        for (int i = 0; i < QG; ++i) gg[i] = ld_pop(G + read_slot<LG, ODD>(id, d, NP, i, false));
+    } else {
+#pragma unroll
+        for (int i = 0; i < QF; ++i) {
+            const bool wall = i > 0 && ((w >> (FBIT + i - 1)) & 1u);
+            f[i] = ld_pop(F + read_slot<LF, ODD>(id, d, NP, i, wall));
         }
 #pragma unroll
-        for (int i = 0; i < LF::Q; ++i) {
-            const bool wall = i > 0 && ((w >> (FBIT + i - 1)) & 1u);
-            T v;
-            if (ODD == wall) v = a.F[(long long)i * NP + id];
-            else v = a.F[(long long)LF::opp(i) * NP + id + off<LF>(d, LF::opp(i))];
-            if (wall) {
-                if (inlet && LF::cx(i) > 0) {
-                    // moving-wall bounce-back with the inlet velocity (rho_w = 1)
-                    v += T(6.0 * LF::w(i) * LF::cx(i)) * uin;
-                } else if (outlet && LF::cx(i) < 0) {
-                    // pressure anti-bounce-back at rho_out with the previous velocity
-                    const T eu = T(LF::cx(i)) * uo0 + T(LF::cy(i)) * uo1 + T(LF::cz(i)) * uo2;
-                    const T uq = uo0 * uo0 + uo1 * uo1 + uo2 * uo2;
-                    v = -v + T(2.0 * LF::w(i)) * (T(p.rho_out) * (T(1) + T(4.5) * eu * eu - T(1.5) * uq) - T(1));
-                }
-            }
-            f[i] = v;
+        for (int i = 0; i < QG; ++i) {
+            const bool wall = i > 0 && ((w >> (GBIT + i - 1)) & 1u);
+            gg[i] = ld_pop(G + read_slot<LG, ODD>(id, d, NP, i, wall));
         }
+        const int face = y + g.ny * z;
+        if constexpr (QF > 0) {
+            if (inlet) {
+                // moving-wall bounce-back with the inlet velocity (rho_w = 1)
+                const T uin = T(a.inlet_ux[face]);
+#pragma unroll
+                for (int i = 1; i < QF; ++i)
+                    if (LF::cx(i) > 0) f[i] += T(6.0 * LF::w(i) * LF::cx(i)) * uin;
+            }
+            if (outlet) {
+                // pressure anti-bounce-back at rho_out with the previous velocity
+                const T uo0 = T(a.side[4 * face + 0]), uo1 = T(a.side[4 * face + 1]), uo2 = T(a.side[4 * face + 2]);
+                const T uq = uo0 * uo0 + uo1 * uo1 + uo2 * uo2;
+#pragma unroll
+                for (int i = 1; i < QF; ++i)
+                    if (LF::cx(i) < 0) {
+                        const T eu = T(LF::cx(i)) * uo0 + T(LF::cy(i)) * uo1 + T(LF::cz(i)) * uo2;
+                        f[i] = -f[i] + T(2.0 * LF::w(i)) * (T(p.rho_out) * (T(1) + T(4.5) * eu * eu - T(1.5) * uq) - T(1));
+                    }
+            }
+        }
+        if (inlet) {
+#pragma unroll
+            for (int i = 1; i < QG; ++i)
+                if (LG::cx(i) > 0) gg[i] = -gg[i] + T(2.0 * gweight<LG>(p, i)) * T(p.c_inlet - p.cref);
+        }
+        if (outlet) {
+            const T co = T(a.side[4 * face + 3]);
+#pragma unroll
+            for (int i = 1; i < QG; ++i)
+                if (LG::cx(i) < 0) gg[i] = -gg[i] + T(2.0 * gweight<LG>(p, i)) * (co - T(p.cref));
+        }
+    }
+
+    T ux = T(0), uy = T(0), uz = T(0), rho = T(1);
+    if constexpr (QF > 0) {
         T s = T(0), jx = T(0), jy = T(0), jz = T(0);
 #pragma unroll
-        for (int i = 0; i < LF::Q; ++i) {
+        for (int i = 0; i < QF; ++i) {
             s += f[i];
             if (LF::cx(i)) jx += T(LF::cx(i)) * f[i];
             if (LF::cy(i)) jy += T(LF::cy(i)) * f[i];
@@ -306,39 +401,20 @@ __global__ void __launch_bounds__(FLUID_BLOCK) k_fluid(const Dev<T> a, const Phy
         ux = jx * inv;
         uy = jy * inv;
         uz = jz * inv;
-        collide_flow<LF, T>(f, rho, ux, uy, uz, p);
+        collide_flow<LF, T>(reinterpret_cast<T(&)[QF]>(f), rho, ux, uy, uz, p);
 #pragma unroll
-        for (int i = 0; i < LF::Q; ++i) {
-            if (ODD) a.F[(long long)i * NP + id + off<LF>(d, i)] = f[i];
-            else a.F[(long long)LF::opp(i) * NP + id] = f[i];
-        }
-    }
-    T gg[LG::Q];
-    const T co = outlet ? T(a.side[4 * face + 3]) : T(0);
-#pragma unroll
-    for (int i = 0; i < LG::Q; ++i) {
-        const bool wall = i > 0 && ((w >> (GBIT + i - 1)) & 1u);
-        T v;
-        if (ODD == wall) v = a.G[(long long)i * NP + id];
-        else v = a.G[(long long)LG::opp(i) * NP + id + off<LG>(d, LG::opp(i))];
-        if (wall) {
-            if (inlet && LG::cx(i) > 0) v = -v + T(2.0 * gweight<LG>(p, i)) * T(p.c_inlet - p.cref);
-            else if (outlet && LG::cx(i) < 0) v = -v + T(2.0 * gweight<LG>(p, i)) * (co - T(p.cref));
-        }
-        gg[i] = v;
+        for (int i = 0; i < QF; ++i) st_pop(F + write_slot<LF, ODD>(id, d, NP, i), f[i]);
     }
     T sc = T(0);
 #pragma unroll
-    for (int i = 0; i < LG::Q; ++i) sc += gg[i];
+    for (int i = 0; i < QG; ++i) sc += gg[i];
     const T C = T(p.cref) + sc;
     if (!(rho > T(0)) || !isfinite(C)) *a.err |= ERR_NUMERIC;
     collide_solute<LG, T>(gg, C, ux, uy, uz, p);
 #pragma unroll
-    for (int i = 0; i < LG::Q; ++i) {
-        if (ODD) a.G[(long long)i * NP + id + off<LG>(d, i)] = gg[i];
-        else a.G[(long long)LG::opp(i) * NP + id] = gg[i];
-    }
+    for (int i = 0; i < QG; ++i) st_pop(G + write_slot<LG, ODD>(id, d, NP, i), gg[i]);
     if (outlet) {
+        const int face = y + g.ny * z;
         a.side[4 * face + 0] = (double)ux;
         a.side[4 * face + 1] = (double)uy;
         a.side[4 * face + 2] = (double)uz;
@@ -376,36 +452,53 @@ __device__ __forceinline__ double warp_sum(double v) {
 // Wet boundary cells (compacted list): solute stream, Eq. general_RBC on each
 // link to a fluid cell (all links from the streamed values), ledger
 // m_l = g_o(new) - g_o(streamed), collision with u = 0, Eq.
-// solidFractionUpdate (adjacent growth, conserving sign).
+// solidFractionUpdate (adjacent growth, conserving sign).  FP64 is used only
+// where the ledger needs it (GB300 runs FP64 at a small fraction of FP32):
+// each m_l is the exact FP64 difference of two stored values, the shares
+// need one division per cell.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t pack_xyz(int x, int y, int z) {
+    return (uint64_t)(uint32_t)x | ((uint64_t)(uint32_t)y << 21) | ((uint64_t)(uint32_t)z << 42);
+}
+__device__ __forceinline__ void unpack_xyz(uint64_t v, int& x, int& y, int& z) {
+    x = (int)(v & 0x1fffffu);
+    y = (int)((v >> 21) & 0x1fffffu);
+    z = (int)((v >> 42) & 0x1fffffu);
+}
+
 template <typename T, class LG, bool ODD>
 __global__ void __launch_bounds__(LIST_BLOCK) k_bound(const Dev<T> a, const Phys p) {
     constexpr int Q = LG::Q;
-    const long long NP = a.geo.NP;
+    const Geo& g = a.geo;
+    const uint32_t NP = (uint32_t)g.NP;
+    T* __restrict__ G = a.G;
     const int n = *a.nb;
     double rsum = 0.0, dsum = 0.0;
     const T cref = T(p.cref);
     const T gam = T(p.gamma), ics2 = T(1.0 / gcs2<LG>(p));
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-        const long long b = a.b_idx[e];
+        int x, y, z;
+        unpack_xyz(a.b_xyz[e], x, y, z);
+        const uint32_t b = (uint32_t)g.idx(x, y, z);
+        const Nbr32 d = nbr32(g, x, y, z);
         const uint32_t bw = a.b_word[e];
         T gp[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const bool inactive = i > 0 && ((bw >> (i - 1)) & 1u);
-            if (i == 0 || ODD == inactive) gp[i] = a.G[(long long)i * NP + b];
-            else gp[i] = a.G[(long long)LG::opp(i) * NP + a.b_nbr[(long long)(LG::opp(i) - 1) * a.cap_b + e]];
+            gp[i] = G[read_slot<LG, ODD>(b, d, NP, i, inactive)];
         }
-        T g[Q];
+        T gq[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) g[i] = gp[i];
+        for (int i = 0; i < Q; ++i) gq[i] = gp[i];
         const bool dir = (bw & BW_DIRICHLET) != 0u;
         const T kr = a.b_krate ? T(a.b_krate[e]) : T(p.k_r);
-        double m[Q];
-        double M = 0.0, S = 0.0;
+        T mabs[Q];
+        double M = 0.0;
+        T S = T(0);
 #pragma unroll
         for (int o = 1; o < Q; ++o) {
-            m[o] = 0.0;
+            mabs[o] = T(0);
             if (!((bw >> (BW_LINK + o - 1)) & 1u)) continue;
             const T gt = gp[LG::opp(o)];
             const T w2 = T(2.0 * gweight<LG>(p, o));
@@ -413,7 +506,7 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_bound(const Dev<T> a, const Phys
             if (dir) {
                 val = -gt + w2 * T(p.c_dir - p.cref);  // anti-bounce-back, C_wall = c_dirichlet
             } else {
-                const T kap = T(a.b_kappa[(long long)(o - 1) * a.cap_b + e]);
+                const T kap = a.b_kappa[(long long)(o - 1) * a.cap_b + e];
                 T k = T(0);
                 bool inf = false;
                 if (p.scheme == 0) k = gam * kr * kap * ics2;
@@ -428,30 +521,24 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_bound(const Dev<T> a, const Phys
                     val = k * ik * w2 * (T(p.c_eq) - cref) + (T(1) - k) * ik * gt;
                 }
             }
-            m[o] = (double)val - (double)gp[o];
-            g[o] = val;
-            M += m[o];
-            S += fabs(m[o]);
+            M += (double)val - (double)gp[o];  // exact
+            mabs[o] = fabs(val - gp[o]);
+            S += mabs[o];
+            gq[o] = val;
         }
         T sc = T(0);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) sc += g[i];
+        for (int i = 0; i < Q; ++i) sc += gq[i];
         const T C = cref + sc;
         if (!isfinite(C)) *a.err |= ERR_NUMERIC;
-        collide_solute<LG, T>(g, C, T(0), T(0), T(0), p);
+        collide_solute<LG, T>(gq, C, T(0), T(0), T(0), p);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            if (ODD) {
-                if (i == 0) a.G[b] = g[0];
-                else a.G[(long long)i * NP + a.b_nbr[(long long)(i - 1) * a.cap_b + e]] = g[i];
-            } else {
-                a.G[(long long)LG::opp(i) * NP + b] = g[i];
-            }
-        }
+        for (int i = 0; i < Q; ++i) G[write_slot<LG, ODD>(b, d, NP, i)] = gq[i];
+        double* sh = a.b_share + e;
         if (dir) {
             dsum += M;
 #pragma unroll
-            for (int o = 1; o < Q; ++o) a.b_share[(long long)(o - 1) * a.cap_b + e] = 0.0;
+            for (int o = 1; o < Q; ++o) sh[(long long)(o - 1) * a.cap_b] = 0.0;
             continue;
         }
         rsum += M;
@@ -460,17 +547,31 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_bound(const Dev<T> a, const Phys
             ph -= p.Vm * M;
             a.phi[b] = ph;
         }
+        const double r = (M < 0.0 && S > T(0)) ? -p.Vm * M / (double)S : 0.0;
 #pragma unroll
-        for (int o = 1; o < Q; ++o)
-            a.b_share[(long long)(o - 1) * a.cap_b + e] = (M < 0.0) ? -p.Vm * M * fabs(m[o]) / S : 0.0;
-        if (p.phase_change && ph <= 0.0)
-            push_event(a.nev, a.cap_e, a.ev_node, a.ev_kind, a.err, (int)b, EV_DISSOLVE);
+        for (int o = 1; o < Q; ++o) sh[(long long)(o - 1) * a.cap_b] = r * (double)mabs[o];
+        if (p.phase_change && ph <= 0.0) push_event(a.nev, a.cap_e, a.ev_node, a.ev_kind, a.err, (int)b, EV_DISSOLVE);
     }
+    // each block owns its two accumulators (fixed grid): no atomics and a
+    // fixed summation order
+    __shared__ double red[2][LIST_BLOCK / 32];
     rsum = warp_sum(rsum);
     dsum = warp_sum(dsum);
-    if ((threadIdx.x & 31) == 0 && (rsum != 0.0 || dsum != 0.0)) {
-        atomicAdd(&a.acc[0], rsum);
-        atomicAdd(&a.acc[1], dsum);
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = rsum;
+        red[1][threadIdx.x >> 5] = dsum;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0, q = 0.0;
+        for (int k = 0; k < LIST_BLOCK / 32; ++k) {
+            r += red[0][k];
+            q += red[1][k];
+        }
+        if (r != 0.0 || q != 0.0) {
+            a.bacc[2 * blockIdx.x] += r;
+            a.bacc[2 * blockIdx.x + 1] += q;
+        }
     }
 }
 
@@ -539,27 +640,30 @@ __device__ __forceinline__ double solid_ind(const Geo& g, const uint8_t* kind, i
 }
 
 // Unit normal n = -grad s / |grad s| of the isotropic gradient
-// cs^-2 sum_i w_i s(x + e_i) e_i (D3Q19 / D2Q9 weights); false if |grad s|
-// is below 1e-12.
+// cs^-2 sum_i w_i s(x + e_i) e_i (D3Q19 / D2Q9 weights), accumulated exactly
+// as the integer vector sum_i (36 w_i) s e_i; false if it vanishes.  Exact
+// accumulation keeps symmetric components exactly zero, which the
+// precipitation-excess split depends on.
 template <int DIM>
 __device__ bool wall_normal(const Geo& g, const uint8_t* kind, int x, int y, int z, double n[3]) {
     using L = typename NormalStencil<DIM>::L;
-    double gx = 0.0, gy = 0.0, gz = 0.0;
+    int gx = 0, gy = 0, gz = 0;
 #pragma unroll
     for (int i = 1; i < L::Q; ++i) {
-        const double s = solid_ind(g, kind, x + L::cx(i), y + L::cy(i), z + L::cz(i));
-        gx += L::w(i) * s * L::cx(i) * 3.0;
-        gy += L::w(i) * s * L::cy(i) * 3.0;
-        gz += L::w(i) * s * L::cz(i) * 3.0;
+        const int s = (int)solid_ind(g, kind, x + L::cx(i), y + L::cy(i), z + L::cz(i));
+        const int wi = (int)(36.0 * L::w(i) + 0.5);
+        gx += wi * s * L::cx(i);
+        gy += wi * s * L::cy(i);
+        gz += wi * s * L::cz(i);
     }
-    const double len = sqrt(gx * gx + gy * gy + gz * gz);
-    if (len < 1e-12) {
+    if (gx == 0 && gy == 0 && gz == 0) {
         n[0] = n[1] = n[2] = 0.0;
         return false;
     }
-    n[0] = -gx / len;
-    n[1] = -gy / len;
-    n[2] = -gz / len;
+    const double len = sqrt((double)(gx * gx + gy * gy + gz * gz));
+    n[0] = -(double)gx / len;
+    n[1] = -(double)gy / len;
+    n[2] = -(double)gz / len;
     return true;
 }
 
@@ -928,16 +1032,15 @@ __global__ void k_write_lists(const Dev<T> a, const Phys p, int which, int force
         if (sel) {
             if (which == 0 && pos < a.cap_b) {
                 a.b_idx[pos] = (int)id;
+                a.b_xyz[pos] = pack_xyz(x, y, z);
                 a.bmap[id] = pos;
                 uint32_t bw = 0;
                 const uint8_t kd = a.kind[id];
                 if (kd == KIND_DIRICHLET) bw |= BW_DIRICHLET;
                 double nrm[3];
                 const bool ok = wall_normal<LG::DIM>(g, a.kind, x, y, z, nrm);
-                const Nbr d = nbr_deltas(g, x, y, z);
 #pragma unroll
                 for (int o = 1; o < LG::Q; ++o) {
-                    a.b_nbr[(long long)(o - 1) * a.cap_b + pos] = id + off<LG>(d, o);
                     int xs = x - LG::cx(o), ys = y - LG::cy(o), zs = z - LG::cz(o);
                     if (class_at<LG>(g, a.kind, xs, ys, zs) == CLS_SOLID) bw |= 1u << (o - 1);
                     int xf = x + LG::cx(o), yf = y + LG::cy(o), zf = z + LG::cz(o);
@@ -1181,9 +1284,16 @@ class Engine final : public ISim {
         g.OFF = 32;
         g.NP = ((g.OFF + (long long)g.SX * g.SY * g.SZ + 64 + 63) / 64) * 64;
         ncell_ = (long long)g.nx * g.ny * g.nz;
-        if (g.NP >= (1LL << 31)) {
-            err = "grid too large for 32-bit cell indices";
+        if (g.nx >= (1 << 21) || g.ny >= (1 << 21) || g.nz >= (1 << 21)) {
+            err = "grid extent must be below 2^21 cells per axis";
             return 1;
+        }
+        {
+            const long long qmax = std::max(LF::Q, LG::Q);
+            if (g.NP >= (1LL << 31) || qmax * g.NP >= (1LL << 32)) {
+                err = "grid too large for 32-bit population indices";
+                return 1;
+            }
         }
         // physics
         Phys& p = ph_;
@@ -1262,7 +1372,7 @@ class Engine final : public ISim {
         LB_CUDA(dalloc(&d_.nb, 1));
         LB_CUDA(dalloc(&d_.b_idx, (size_t)d_.cap_b));
         LB_CUDA(dalloc(&d_.b_word, (size_t)d_.cap_b));
-        LB_CUDA(dalloc(&d_.b_nbr, (size_t)(QG - 1) * d_.cap_b));
+        LB_CUDA(dalloc(&d_.b_xyz, (size_t)d_.cap_b));
         LB_CUDA(dalloc(&d_.b_kappa, (size_t)(QG - 1) * d_.cap_b));
         LB_CUDA(dalloc(&d_.b_share, (size_t)(QG - 1) * d_.cap_b));
         LB_CUDA(dalloc(&d_.bmap, (size_t)NP));
@@ -1286,6 +1396,9 @@ class Engine final : public ISim {
         }
         LB_CUDA(dalloc(&d_.step, 1));
         LB_CUDA(dalloc(&d_.acc, 4));
+        nbacc_ = list_grid(d_.cap_b);
+        LB_CUDA(dalloc(&d_.bacc, (size_t)2 * nbacc_));
+        LB_CUDA(cudaMemset(d_.bacc, 0, 2 * nbacc_ * sizeof(double)));
         LB_CUDA(dalloc(&d_.err, 1));
         LB_CUDA(dalloc(&d_.blk, (size_t)nchunks_ + 1));
         LB_CUDA(cudaStreamCreateWithFlags(&own_, cudaStreamNonBlocking));
@@ -1443,9 +1556,15 @@ class Engine final : public ISim {
         k_reduce_final<0><<<1, 32, 0, own_>>>(part, nblk, part + 2 * nblk);
         LB_CUDA(cudaGetLastError());
         double sums[2], acc[4];
+        std::vector<double> bacc((size_t)2 * nbacc_);
         LB_CUDA(cudaMemcpyAsync(sums, part + 2 * nblk, 2 * sizeof(double), cudaMemcpyDeviceToHost, own_));
         LB_CUDA(cudaMemcpyAsync(acc, d_.acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, own_));
+        LB_CUDA(cudaMemcpyAsync(bacc.data(), d_.bacc, bacc.size() * sizeof(double), cudaMemcpyDeviceToHost, own_));
         LB_CUDA(cudaStreamSynchronize(own_));
+        for (int b = 0; b < nbacc_; ++b) {
+            acc[0] += bacc[2 * b];
+            acc[1] += bacc[2 * b + 1];
+        }
         cudaFree(part);
         out[0] = sums[0];
         out[1] = prm_.molar_volume > 0.0 ? sums[1] / prm_.molar_volume : 0.0;
@@ -1464,9 +1583,15 @@ class Engine final : public ISim {
         k_reduce_final<0><<<1, 32, 0, own_>>>(part, nblk, part + 2 * nblk);
         LB_CUDA(cudaGetLastError());
         double sums[2], acc[4];
+        std::vector<double> bacc((size_t)2 * nbacc_);
         LB_CUDA(cudaMemcpyAsync(sums, part + 2 * nblk, 2 * sizeof(double), cudaMemcpyDeviceToHost, own_));
         LB_CUDA(cudaMemcpyAsync(acc, d_.acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, own_));
+        LB_CUDA(cudaMemcpyAsync(bacc.data(), d_.bacc, bacc.size() * sizeof(double), cudaMemcpyDeviceToHost, own_));
         LB_CUDA(cudaStreamSynchronize(own_));
+        for (int b = 0; b < nbacc_; ++b) {
+            acc[0] += bacc[2 * b];
+            acc[1] += bacc[2 * b + 1];
+        }
         out[0] = sums[0];
         out[1] = prm_.molar_volume > 0.0 ? sums[1] / prm_.molar_volume : 0.0;
         out[2] = acc[2];
@@ -1708,6 +1833,7 @@ class Engine final : public ISim {
     Phys ph_{};
     long long ncell_ = 0, nfluid_ = 0, nb0_ = 0;
     int nchunks_ = 0;
+    int nbacc_ = 0;
     int lastodd_ = 1;
     int64_t steps_ = 0;
     cudaStream_t own_ = nullptr, last_stream_ = nullptr;

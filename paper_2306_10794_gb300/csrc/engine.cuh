@@ -149,7 +149,7 @@ struct Dev {
     uint64_t* b_xyz;      // packed cell coordinates (21 bits each)
     T* b_kappa;           // (QG-1) * cap_b
     double* b_krate;      // cap_b or null
-    double* b_share;      // (QG-1) * cap_b
+    T* b_share;           // (QG-1) * cap_b, precipitation shares (storage precision)
     int* bmap;            // NP
     // fluid cells receiving precipitation shares
     int cap_f;
@@ -448,6 +448,39 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// Exact sum of differences of stored populations.  FP64 storage: plain FP64.
+// FP32 storage: float-float accumulation (TwoSum), exact for the differences
+// and accurate to ~2^-48 for the sum, converted to FP64 once per cell, so the
+// FP32 path issues almost no FP64 instructions (GB300 runs FP64 at a small
+// fraction of the FP32 rate).
+template <typename T>
+struct DiffSum {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { s += a - b; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct DiffSum<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float d = a - b;  // a - b = d + e exactly
+        const float bv = d - a;
+        const float e = (a - (d - bv)) + (-b - bv);
+        const float s2 = hi + d;  // hi + d = s2 + t exactly
+        const float bb = s2 - hi;
+        const float t = (hi - (s2 - bb)) + (d - bb);
+        const float tl = t + (lo + e);
+        hi = s2 + tl;
+        lo = tl - (hi - s2);
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// phi <= 0 and phi >= 1 on the bit pattern of a (non-NaN) double: integer
+// compares, no FP64 instruction.
+__device__ __forceinline__ bool dle0(double v) { return __double_as_longlong(v) <= 0LL; }
+__device__ __forceinline__ bool dge1(double v) { return __double_as_longlong(v) >= 0x3FF0000000000000LL; }
+
 // ---------------------------------------------------------------------------
 // Wet boundary cells (compacted list): solute stream, Eq. general_RBC on each
 // link to a fluid cell (all links from the streamed values), ledger
@@ -494,7 +527,7 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_bound(const Dev<T> a, const Phys
         const bool dir = (bw & BW_DIRICHLET) != 0u;
         const T kr = a.b_krate ? T(a.b_krate[e]) : T(p.k_r);
         T mabs[Q];
-        double M = 0.0;
+        DiffSum<T> ms;
         T S = T(0);
 #pragma unroll
         for (int o = 1; o < Q; ++o) {
@@ -521,7 +554,7 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_bound(const Dev<T> a, const Phys
                     val = k * ik * w2 * (T(p.c_eq) - cref) + (T(1) - k) * ik * gt;
                 }
             }
-            M += (double)val - (double)gp[o];  // exact
+            ms.add(val, gp[o]);
             mabs[o] = fabs(val - gp[o]);
             S += mabs[o];
             gq[o] = val;
@@ -534,23 +567,27 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_bound(const Dev<T> a, const Phys
         collide_solute<LG, T>(gq, C, T(0), T(0), T(0), p);
 #pragma unroll
         for (int i = 0; i < Q; ++i) G[write_slot<LG, ODD>(b, d, NP, i)] = gq[i];
-        double* sh = a.b_share + e;
+        const double M = ms.value();
+        T* sh = a.b_share + e;
         if (dir) {
             dsum += M;
 #pragma unroll
-            for (int o = 1; o < Q; ++o) sh[(long long)(o - 1) * a.cap_b] = 0.0;
+            for (int o = 1; o < Q; ++o) sh[(long long)(o - 1) * a.cap_b] = T(0);
             continue;
         }
         rsum += M;
-        double ph = a.phi[b];
-        if (M > 0.0) {
+        const bool diss = __double_as_longlong(M) > 0LL;   // M > 0
+        const bool prec = __double_as_longlong(M) < 0LL && (__double_as_longlong(M) << 1) != 0LL;  // M < 0
+        double ph = 0.0;
+        if (diss || p.phase_change) ph = a.phi[b];
+        if (diss) {
             ph -= p.Vm * M;
             a.phi[b] = ph;
         }
-        const double r = (M < 0.0 && S > T(0)) ? -p.Vm * M / (double)S : 0.0;
+        const T r = (prec && S > T(0)) ? T(-p.Vm) * T(M) / S : T(0);
 #pragma unroll
-        for (int o = 1; o < Q; ++o) sh[(long long)(o - 1) * a.cap_b] = r * (double)mabs[o];
-        if (p.phase_change && ph <= 0.0) push_event(a.nev, a.cap_e, a.ev_node, a.ev_kind, a.err, (int)b, EV_DISSOLVE);
+        for (int o = 1; o < Q; ++o) sh[(long long)(o - 1) * a.cap_b] = r * mabs[o];
+        if (p.phase_change && dle0(ph)) push_event(a.nev, a.cap_e, a.ev_node, a.ev_kind, a.err, (int)b, EV_DISSOLVE);
     }
     // each block owns its two accumulators (fixed grid): no atomics and a
     // fixed summation order
@@ -582,18 +619,18 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_fend(const Dev<T> a, const Phys 
     const int n = *a.nf;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
         const long long f = a.f_idx[e];
-        double acc = 0.0;
+        T acc = T(0);
 #pragma unroll
         for (int o = 1; o < LG::Q; ++o) {
             const int s = a.f_src[(long long)(o - 1) * a.cap_f + e];
             if (s >= 0) acc += a.b_share[(long long)(o - 1) * a.cap_b + s];
         }
         double ph = a.phi[f];
-        if (acc != 0.0) {
-            ph += acc;
+        if (acc != T(0)) {
+            ph += (double)acc;
             a.phi[f] = ph;
         }
-        if (p.phase_change && ph >= 1.0)
+        if (p.phase_change && dge1(ph))
             push_event(a.nev, a.cap_e, a.ev_node, a.ev_kind, a.err, (int)f, EV_PRECIPITATE);
     }
 }

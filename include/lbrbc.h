@@ -150,6 +150,28 @@ lbrbc_status lbrbc_classes(lbrbc_sim *sim, uint8_t *out);
  * `out` is host memory with room for 6 doubles. */
 lbrbc_status lbrbc_mass_ledger(lbrbc_sim *sim, double *out);
 
+/* lbrbc_mass_ledger without allocating device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc / cudaFree at this point -- for instance a host program that has
+ * handed the GPU's memory to its own pool allocator (a fresh cudaMalloc could
+ * fail or fragment it), or a monitoring loop that must not trigger the
+ * device-wide synchronisation cudaFree implies.  It returns the same six
+ * values as lbrbc_mass_ledger (summation order differs: agreement to
+ * round-off).
+ *   - Scratch: a file-scope device array of 2 * 4096 + 8 doubles (65.6 KB),
+ *     present on every GPU that loads the library until the process exits.
+ *     Partial sums are kept per block of 65536 cells, so grids above
+ *     4096 * 65536 = 268435456 cells are rejected with LBRBC_ERR_ARG.
+ *   - The first call on a device looks up the array's device address (with
+ *     the simulation's device made current); make that first call before any
+ *     stream capture.
+ *   - Every call on a device shares the array and leaves its last contents
+ *     there; each call overwrites every entry it reads, so nothing needs
+ *     clearing.  Calls that overlap on the GPU (two host threads, two
+ *     simulations on one device at once) race on it: serialise them.
+ *   - Synchronises the stream of the last lbrbc_step.  `out`: host, 6 doubles. */
+lbrbc_status lbrbc_mass_ledger_noalloc(lbrbc_sim *sim, double *out);
+
 /* Phase-change events logged so far (up to event_log_capacity): on return
  * *count holds the number logged; if step/node/kind are non-NULL the first
  * min(*count, capacity) entries are written (host).  kind: 1 dissolution,

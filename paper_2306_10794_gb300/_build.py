@@ -15,7 +15,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 OBJ_DIR = os.path.join(HERE, "_lib", "obj")
 LIB = os.path.join(OUT_DIR, "liblbrbc.so")
-UNITS = ["lbrbc_3d.cu", "lbrbc_2d.cu", "lbrbc_capi.cu"]
+UNITS = ["lbrbc_3d.cu", "lbrbc_2d.cu", "lbrbc_capi.cu", "lbrbc_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC"]
 

@@ -1285,6 +1285,25 @@ __global__ void k_reduce_final(const double* part, int nblocks, double* out) {
     }
 }
 
+// Sum of k_bound's per-block ledger partials and the event-path accumulators
+// (one warp, fixed order): out[0] reacted, out[1] Dirichlet inflow, out[2]
+// unpaid.
+template <int UNUSED = 0>
+__global__ void k_sum_partials(const double* bacc, int nblocks, const double* acc, double* out) {
+    double r = 0.0, q = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += 32) {
+        r += bacc[2 * b];
+        q += bacc[2 * b + 1];
+    }
+    r = warp_sum(r);
+    q = warp_sum(q);
+    if (threadIdx.x == 0) {
+        out[0] = acc[0] + r;
+        out[1] = acc[1] + q;
+        out[2] = acc[2];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Host side of the engine.
 // ---------------------------------------------------------------------------
@@ -1634,6 +1653,35 @@ class Engine final : public ISim {
         out[2] = acc[2];
         out[3] = acc[1];
         out[4] = acc[0];
+        out[5] = (double)steps_;
+        return 0;
+    }
+
+    // Mass balance with caller-provided device scratch and no allocation:
+    // one partial pair per block of cells_per_block cells, then the final
+    // sums; scratch holds 2 * max_blocks + 8 doubles.
+    int ledger_scratch(double* out, double* scratch, int max_blocks, long long cells_per_block,
+                       std::string& err) override {
+        const long long nblk = (ncell_ + cells_per_block - 1) / cells_per_block;
+        if (nblk > max_blocks) {
+            err = "grid of " + std::to_string(ncell_) + " cells exceeds the static scratch of this entry point (" +
+                  std::to_string((long long)max_blocks * cells_per_block) + " cells)";
+            return 1;
+        }
+        LB_CUDA(cudaStreamSynchronize(last_stream_ ? last_stream_ : own_));
+        double* tail = scratch + 2 * (size_t)max_blocks;
+        k_reduce_partial<T, LG><<<(int)nblk, RED_BLOCK, 0, own_>>>(d_, ph_, lastodd_, scratch);
+        k_reduce_final<0><<<1, 32, 0, own_>>>(scratch, (int)nblk, tail);
+        k_sum_partials<0><<<1, 32, 0, own_>>>(d_.bacc, nbacc_, d_.acc, tail + 2);
+        LB_CUDA(cudaGetLastError());
+        double h[5];
+        LB_CUDA(cudaMemcpyAsync(h, tail, 5 * sizeof(double), cudaMemcpyDeviceToHost, own_));
+        LB_CUDA(cudaStreamSynchronize(own_));
+        out[0] = h[0];
+        out[1] = prm_.molar_volume > 0.0 ? h[1] / prm_.molar_volume : 0.0;
+        out[2] = h[4];
+        out[3] = h[3];
+        out[4] = h[2];
         out[5] = (double)steps_;
         return 0;
     }

@@ -23,6 +23,8 @@ class ISim {
                        std::string& err) = 0;
     virtual int check(std::string& err) = 0;
     virtual int profile(int64_t n, cudaStream_t s, double* ms, std::string& err) = 0;
+    virtual int ledger_scratch(double* out, double* scratch, int max_blocks, long long cells_per_block,
+                               std::string& err) = 0;
     virtual int launches_per_step() const = 0;
     virtual long long fluid_cells() const = 0;
     virtual long long boundary_cells() const = 0;

@@ -54,6 +54,7 @@ class LbrbcError(RuntimeError):
 _lib = None
 
 EXPORTED = ["lbrbc_create", "lbrbc_step", "lbrbc_fields", "lbrbc_classes", "lbrbc_mass_ledger",
+            "lbrbc_mass_ledger_noalloc",
             "lbrbc_events", "lbrbc_profile_step", "lbrbc_info", "lbrbc_check", "lbrbc_last_error",
             "lbrbc_destroy"]
 
@@ -78,6 +79,8 @@ def load(path: str = LIB_PATH):
     lib.lbrbc_classes.argtypes = [vp, P(ctypes.c_uint8)]
     lib.lbrbc_mass_ledger.restype = ctypes.c_int
     lib.lbrbc_mass_ledger.argtypes = [vp, dp]
+    lib.lbrbc_mass_ledger_noalloc.restype = ctypes.c_int
+    lib.lbrbc_mass_ledger_noalloc.argtypes = [vp, dp]
     lib.lbrbc_events.restype = ctypes.c_int
     lib.lbrbc_events.argtypes = [vp, P(ctypes.c_int64), ctypes.c_int64, P(ctypes.c_int64), P(ctypes.c_int64),
                                  P(ctypes.c_int32)]
@@ -139,6 +142,14 @@ def lbrbc_mass_ledger(handle):
     lib = load()
     out = np.zeros(6)
     _check(lib, handle, lib.lbrbc_mass_ledger(handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
+
+
+def lbrbc_mass_ledger_noalloc(handle):
+    """Same values as lbrbc_mass_ledger, computed without device allocation."""
+    lib = load()
+    out = np.zeros(6)
+    _check(lib, handle, lib.lbrbc_mass_ledger_noalloc(handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return out
 
 

@@ -130,6 +130,19 @@ struct Phys {
     int scheme, phase_change;
 };
 
+// The same parameters in the storage precision, precomputed on the host so
+// that per-cell arithmetic never converts from FP64 (FP64 is slow on GB300).
+template <typename T>
+struct PhysT {
+    T f_sym, f_anti;   // flow relaxation rates
+    T g_sym, g_anti;   // solute relaxation rates
+    T gw[9];           // solute weights per direction
+    T ics2;            // 1 / cs^2 of the solute lattice
+    T cref;            // deviation reference
+    T c_in_d, c_dir_d, c_eq_d;  // c_inlet, c_dirichlet, c_eq minus cref
+    T rho_out, k_r, gamma, neg_vm;
+};
+
 template <typename T>
 struct Dev {
     Geo geo;
@@ -194,11 +207,12 @@ __device__ __forceinline__ double gcs2(const Phys& p) {
 // Collision helpers (deviation form: a_i stores value_i - w_i * ref).
 // ---------------------------------------------------------------------------
 template <class L, typename T>
-__device__ __forceinline__ void collide_flow(T (&f)[L::Q], T rho, T ux, T uy, T uz, const Phys& p) {
+__device__ __forceinline__ void collide_flow(T (&f)[L::Q], T rho, T ux, T uy, T uz, const Phys& p,
+                                             const PhysT<T>& q) {
     const T usq = ux * ux + uy * uy + uz * uz;
     const T drho = rho - T(1);
     if (!p.trt_f) {
-        const T om = T(p.of_sym);
+        const T om = q.f_sym;
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
             const T eu = T(L::cx(i)) * ux + T(L::cy(i)) * uy + T(L::cz(i)) * uz;
@@ -206,7 +220,7 @@ __device__ __forceinline__ void collide_flow(T (&f)[L::Q], T rho, T ux, T uy, T 
             f[i] = f[i] - om * (f[i] - feq);
         }
     } else {
-        const T op = T(p.of_sym), om = T(p.of_anti);
+        const T op = q.f_sym, om = q.f_anti;
         {
             const T feq = T(L::w(0)) * (drho - rho * T(1.5) * usq);
             f[0] = f[0] - op * (f[0] - feq);
@@ -226,26 +240,27 @@ __device__ __forceinline__ void collide_flow(T (&f)[L::Q], T rho, T ux, T uy, T 
 }
 
 template <class L, typename T>
-__device__ __forceinline__ void collide_solute(T (&g)[L::Q], T C, T ux, T uy, T uz, const Phys& p) {
-    const T dc = C - T(p.cref);
-    const T ics2 = T(1.0 / gcs2<L>(p));
+__device__ __forceinline__ void collide_solute(T (&g)[L::Q], T C, T ux, T uy, T uz, const Phys& p,
+                                               const PhysT<T>& q) {
+    const T dc = C - q.cref;
+    const T ics2 = q.ics2;
     if (!p.trt_g) {
-        const T om = T(p.og_anti);
+        const T om = q.g_anti;
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
             const T eu = T(L::cx(i)) * ux + T(L::cy(i)) * uy + T(L::cz(i)) * uz;
-            const T w = T(gweight<L>(p, i));
+            const T w = q.gw[i];
             const T geq = w * dc + w * C * eu * ics2;
             g[i] = g[i] - om * (g[i] - geq);
         }
     } else {
-        const T os = T(p.og_sym), oa = T(p.og_anti);
-        g[0] = g[0] - os * (g[0] - T(gweight<L>(p, 0)) * dc);
+        const T os = q.g_sym, oa = q.g_anti;
+        g[0] = g[0] - os * (g[0] - q.gw[0] * dc);
 #pragma unroll
         for (int i = 1; i <= L::H; ++i) {
             const int j = L::opp(i);
             const T eu = T(L::cx(i)) * ux + T(L::cy(i)) * uy + T(L::cz(i)) * uz;
-            const T w = T(gweight<L>(p, i));
+            const T w = q.gw[i];
             const T ep = w * dc, em = w * C * eu * ics2;
             const T gp = T(0.5) * (g[i] + g[j]), gm = T(0.5) * (g[i] - g[j]);
             const T dp = os * (gp - ep), dm = oa * (gm - em);
@@ -317,7 +332,7 @@ __device__ __forceinline__ void st_pop(T* p, T v) {
 }
 
 template <typename T, class LF, class LG, bool ODD>
-__global__ void __launch_bounds__(FLUID_BLOCK) k_fluid(const Dev<T> a, const Phys p) {
+__global__ void __launch_bounds__(FLUID_BLOCK) k_fluid(const Dev<T> a, const Phys p, const PhysT<T> q) {
     constexpr int QF = LF::Q, QG = LG::Q;
     const Geo& g = a.geo;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -369,20 +384,20 @@ __global__ void __launch_bounds__(FLUID_BLOCK) k_fluid(const Dev<T> a, const Phy
                 for (int i = 1; i < QF; ++i)
                     if (LF::cx(i) < 0) {
                         const T eu = T(LF::cx(i)) * uo0 + T(LF::cy(i)) * uo1 + T(LF::cz(i)) * uo2;
-                        f[i] = -f[i] + T(2.0 * LF::w(i)) * (T(p.rho_out) * (T(1) + T(4.5) * eu * eu - T(1.5) * uq) - T(1));
+                        f[i] = -f[i] + T(2.0 * LF::w(i)) * (q.rho_out * (T(1) + T(4.5) * eu * eu - T(1.5) * uq) - T(1));
                     }
             }
         }
         if (inlet) {
 #pragma unroll
             for (int i = 1; i < QG; ++i)
-                if (LG::cx(i) > 0) gg[i] = -gg[i] + T(2.0 * gweight<LG>(p, i)) * T(p.c_inlet - p.cref);
+                if (LG::cx(i) > 0) gg[i] = -gg[i] + T(2) * q.gw[i] * q.c_in_d;
         }
         if (outlet) {
             const T co = T(a.side[4 * face + 3]);
 #pragma unroll
             for (int i = 1; i < QG; ++i)
-                if (LG::cx(i) < 0) gg[i] = -gg[i] + T(2.0 * gweight<LG>(p, i)) * (co - T(p.cref));
+                if (LG::cx(i) < 0) gg[i] = -gg[i] + T(2) * q.gw[i] * (co - q.cref);
         }
     }
 
@@ -401,16 +416,16 @@ __global__ void __launch_bounds__(FLUID_BLOCK) k_fluid(const Dev<T> a, const Phy
         ux = jx * inv;
         uy = jy * inv;
         uz = jz * inv;
-        collide_flow<LF, T>(reinterpret_cast<T(&)[QF]>(f), rho, ux, uy, uz, p);
+        collide_flow<LF, T>(reinterpret_cast<T(&)[QF]>(f), rho, ux, uy, uz, p, q);
 #pragma unroll
         for (int i = 0; i < QF; ++i) st_pop(F + write_slot<LF, ODD>(id, d, NP, i), f[i]);
     }
     T sc = T(0);
 #pragma unroll
     for (int i = 0; i < QG; ++i) sc += gg[i];
-    const T C = T(p.cref) + sc;
+    const T C = q.cref + sc;
     if (!(rho > T(0)) || !isfinite(C)) *a.err |= ERR_NUMERIC;
-    collide_solute<LG, T>(gg, C, ux, uy, uz, p);
+    collide_solute<LG, T>(gg, C, ux, uy, uz, p, q);
 #pragma unroll
     for (int i = 0; i < QG; ++i) st_pop(G + write_slot<LG, ODD>(id, d, NP, i), gg[i]);
     if (outlet) {
@@ -500,15 +515,15 @@ __device__ __forceinline__ void unpack_xyz(uint64_t v, int& x, int& y, int& z) {
 }
 
 template <typename T, class LG, bool ODD>
-__global__ void __launch_bounds__(LIST_BLOCK) k_bound(const Dev<T> a, const Phys p) {
+__global__ void __launch_bounds__(LIST_BLOCK) k_bound(const Dev<T> a, const Phys p, const PhysT<T> q) {
     constexpr int Q = LG::Q;
     const Geo& g = a.geo;
     const uint32_t NP = (uint32_t)g.NP;
     T* __restrict__ G = a.G;
     const int n = *a.nb;
     double rsum = 0.0, dsum = 0.0;
-    const T cref = T(p.cref);
-    const T gam = T(p.gamma), ics2 = T(1.0 / gcs2<LG>(p));
+    const T cref = q.cref;
+    const T gam = q.gamma, ics2 = q.ics2;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
         int x, y, z;
         unpack_xyz(a.b_xyz[e], x, y, z);
@@ -525,7 +540,7 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_bound(const Dev<T> a, const Phys
 #pragma unroll
         for (int i = 0; i < Q; ++i) gq[i] = gp[i];
         const bool dir = (bw & BW_DIRICHLET) != 0u;
-        const T kr = a.b_krate ? T(a.b_krate[e]) : T(p.k_r);
+        const T kr = a.b_krate ? T(a.b_krate[e]) : q.k_r;
         T mabs[Q];
         DiffSum<T> ms;
         T S = T(0);
@@ -534,10 +549,10 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_bound(const Dev<T> a, const Phys
             mabs[o] = T(0);
             if (!((bw >> (BW_LINK + o - 1)) & 1u)) continue;
             const T gt = gp[LG::opp(o)];
-            const T w2 = T(2.0 * gweight<LG>(p, o));
+            const T w2 = T(2) * q.gw[o];
             T val;
             if (dir) {
-                val = -gt + w2 * T(p.c_dir - p.cref);  // anti-bounce-back, C_wall = c_dirichlet
+                val = -gt + w2 * q.c_dir_d;  // anti-bounce-back, C_wall = c_dirichlet
             } else {
                 const T kap = a.b_kappa[(long long)(o - 1) * a.cap_b + e];
                 T k = T(0);
@@ -548,10 +563,10 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_bound(const Dev<T> a, const Phys
                     if (kap > T(0)) k = gam * kr * ics2 / kap;
                     else inf = true;
                 } else inf = true;
-                if (inf) val = -gt + w2 * (T(p.c_eq) - cref);
+                if (inf) val = -gt + w2 * q.c_eq_d;
                 else {
                     const T ik = T(1) / (T(1) + k);
-                    val = k * ik * w2 * (T(p.c_eq) - cref) + (T(1) - k) * ik * gt;
+                    val = k * ik * w2 * q.c_eq_d + (T(1) - k) * ik * gt;
                 }
             }
             ms.add(val, gp[o]);
@@ -564,7 +579,7 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_bound(const Dev<T> a, const Phys
         for (int i = 0; i < Q; ++i) sc += gq[i];
         const T C = cref + sc;
         if (!isfinite(C)) *a.err |= ERR_NUMERIC;
-        collide_solute<LG, T>(gq, C, T(0), T(0), T(0), p);
+        collide_solute<LG, T>(gq, C, T(0), T(0), T(0), p, q);
 #pragma unroll
         for (int i = 0; i < Q; ++i) G[write_slot<LG, ODD>(b, d, NP, i)] = gq[i];
         const double M = ms.value();
@@ -584,7 +599,7 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_bound(const Dev<T> a, const Phys
             ph -= p.Vm * M;
             a.phi[b] = ph;
         }
-        const T r = (prec && S > T(0)) ? T(-p.Vm) * T(M) / S : T(0);
+        const T r = (prec && S > T(0)) ? q.neg_vm * T(M) / S : T(0);
 #pragma unroll
         for (int o = 1; o < Q; ++o) sh[(long long)(o - 1) * a.cap_b] = r * mabs[o];
         if (p.phase_change && dle0(ph)) push_event(a.nev, a.cap_e, a.ev_node, a.ev_kind, a.err, (int)b, EV_DISSOLVE);
@@ -1387,6 +1402,24 @@ class Engine final : public ISim {
         p.rho_init = P.rho_init;
         p.scheme = P.scheme;
         p.phase_change = P.phase_change;
+        {
+            PhysT<T>& q = pt_;
+            q.f_sym = T(p.of_sym);
+            q.f_anti = T(p.of_anti);
+            q.g_sym = T(p.og_sym);
+            q.g_anti = T(p.og_anti);
+            for (int i = 0; i < 9; ++i) q.gw[i] = T(0);
+            for (int i = 0; i < LG::Q; ++i) q.gw[i] = T(LG::Q == 9 ? LG::w(i) : (i == 0 ? p.gw0 : p.gw1));
+            q.ics2 = T(1.0 / p.gcs2);
+            q.cref = T(p.cref);
+            q.c_in_d = T(p.c_inlet - p.cref);
+            q.c_dir_d = T(p.c_dir - p.cref);
+            q.c_eq_d = T(p.c_eq - p.cref);
+            q.rho_out = T(p.rho_out);
+            q.k_r = T(p.k_r);
+            q.gamma = T(p.gamma);
+            q.neg_vm = T(-p.Vm);
+        }
 
         // kinds with ghosts, host side
         const long long NP = g.NP;
@@ -1806,12 +1839,12 @@ class Engine final : public ISim {
         const Geo& g = d_.geo;
         dim3 grid((g.nx + FLUID_BLOCK - 1) / FLUID_BLOCK, g.ny, g.nz);
         if (ev) LB_CUDA(cudaEventRecord(ev[0], st));
-        if (odd) k_fluid<T, LF, LG, true><<<grid, FLUID_BLOCK, 0, st>>>(d_, ph_);
-        else k_fluid<T, LF, LG, false><<<grid, FLUID_BLOCK, 0, st>>>(d_, ph_);
+        if (odd) k_fluid<T, LF, LG, true><<<grid, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_);
+        else k_fluid<T, LF, LG, false><<<grid, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_);
         if (ev) LB_CUDA(cudaEventRecord(ev[1], st));
         const int lg = list_grid(d_.cap_b);
-        if (odd) k_bound<T, LG, true><<<lg, LIST_BLOCK, 0, st>>>(d_, ph_);
-        else k_bound<T, LG, false><<<lg, LIST_BLOCK, 0, st>>>(d_, ph_);
+        if (odd) k_bound<T, LG, true><<<lg, LIST_BLOCK, 0, st>>>(d_, ph_, pt_);
+        else k_bound<T, LG, false><<<lg, LIST_BLOCK, 0, st>>>(d_, ph_, pt_);
         if (ev) LB_CUDA(cudaEventRecord(ev[2], st));
         k_fend<T, LG><<<list_grid(d_.cap_f), LIST_BLOCK, 0, st>>>(d_, ph_);
         if (ev) LB_CUDA(cudaEventRecord(ev[3], st));
@@ -1916,6 +1949,7 @@ class Engine final : public ISim {
     lbrbc_params prm_{};
     Dev<T> d_{};
     Phys ph_{};
+    PhysT<T> pt_{};
     long long ncell_ = 0, nfluid_ = 0, nb0_ = 0;
     int nchunks_ = 0;
     int nbacc_ = 0;

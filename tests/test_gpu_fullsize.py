@@ -1,0 +1,112 @@
+"""Parity at the workloads' full sizes, through the same C-ABI calls and CUDA
+graphs the benchmark times.
+
+* 2D reactive wall, 128x64 D2Q9, FP64, the full 5000 steps: every cell
+  against the oracle.
+* 3D tilted channel 256x128x128 (the benchmark's workload), FP32 and FP64:
+  every cell against the oracle after a few steps (the oracle needs ~3 s per
+  step at this size).
+* 512^3 sphere pack with phase change: the oracle cannot run the full grid,
+  so it runs a cropped block; after n steps a cell depends only on cells
+  within distance n (plus two rings for the node classes and normals), so
+  the crop's interior beyond that margin must agree cell by cell.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2306_10794_gb300 import lbrbc, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2306_10794_gb300 import _build
+
+    _build.build()
+    oracle.build()
+
+
+def rel_l2(a, b):
+    return float(np.sqrt(((a - b) ** 2).sum() / max((b ** 2).sum(), 1e-300)))
+
+
+def test_wall_2d_full_run_fp64():
+    p, mask, _ = workloads.case_wall_2d(nx=128, ny=64, tau=0.8, solute_q=9)
+    p["precision"] = "fp64"
+    g = lbrbc.Sim(p, mask)
+    o = oracle.OracleSim(p, mask)
+    g.step(5000)
+    o.step(5000)
+    cg, co = g.fields()[2], o.fields()[2]
+    assert np.abs(cg - co).max() < 1e-11
+    # transient from c = 0 towards the steady profile (1 + y/63)/2: c rises
+    # monotonically from the reactive wall to the Dirichlet row
+    col = cg[0, :, 0]
+    assert np.all(np.diff(col) > 0) and 0.0 < col[0] < 0.5 and abs(col[-1] - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("precision,theta", [("fp32", 30.0), ("fp64", 30.0), ("fp64", 45.0)])
+def test_channel_full_size(precision, theta):
+    p, mask, extra = workloads.case_channel(nx=256, ny=128, nz=128, theta_deg=theta, Pe=10.0, Da=1.0)
+    p["precision"] = precision
+    g = lbrbc.Sim(p, mask, **extra)
+    o = oracle.OracleSim(p, mask, **extra)
+    n = 3
+    g.step(n)
+    o.step(n)
+    ug, rg, cg, pg = g.fields()
+    uo, ro, co, po = o.fields()
+    if precision == "fp64":
+        for a, b in ((ug, uo), (rg, ro), (cg, co), (pg, po)):
+            assert np.abs(a - b).max() < 1e-11
+    else:
+        assert rel_l2(cg, co) < 1e-5 and rel_l2(ug, uo) < 1e-5
+        assert np.abs(pg - po).max() < 1e-6
+
+
+@functools.lru_cache(maxsize=1)
+def _pack512():
+    return workloads.case_sphere_pack(n=512, molar_volume=0.05)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_sphere_pack_512_cropped(precision):
+    n_steps = 6
+    p, mask, extra = _pack512()
+    p = dict(p)
+    p["precision"] = precision
+    g = lbrbc.Sim(p, mask, **extra)
+    g.step(n_steps)
+    N = mask.size
+    c = np.empty(N)
+    phi = np.empty(N)
+    lbrbc.lbrbc_fields(g._h, None, None, c, phi)
+    u = np.empty(3 * N)
+    lbrbc.lbrbc_fields(g._h, u, None, None, None)
+    g.close()
+    c = c.reshape(mask.shape)
+    u = u.reshape(mask.shape + (3,))
+    # crops: one at the inlet (open x face inside the crop), one in the interior
+    m = n_steps + 3
+    S = 40
+    for (z0, y0, x0) in ((200, 300, 0), (100, 37, 250)):
+        sub = np.ascontiguousarray(mask[z0:z0 + S, y0:y0 + S, x0:x0 + S])
+        q = dict(p)
+        q.update(nx=S, ny=S, nz=S, bc=("open" if x0 == 0 else "wall", "wall", "wall"))
+        o = oracle.OracleSim(q, sub)
+        o.step(n_steps)
+        uo, _, co, _ = o.fields()
+        lo_x = 0 if x0 == 0 else m
+        core = (slice(m, S - m), slice(m, S - m), slice(lo_x, S - m))
+        cg = c[z0:z0 + S, y0:y0 + S, x0:x0 + S][core]
+        ug = u[z0:z0 + S, y0:y0 + S, x0:x0 + S][core]
+        if precision == "fp64":
+            assert np.abs(cg - co[core]).max() < 1e-11
+            assert np.abs(ug - uo[core]).max() < 1e-12
+        else:
+            assert rel_l2(cg, co[core]) < 1e-5
+            assert np.abs(ug - uo[core]).max() < 1e-7

@@ -193,6 +193,44 @@ lbrbc_status lbrbc_profile_step(lbrbc_sim *sim, int64_t n, void *stream, double 
  * launches per time step (host memory, 3 entries). */
 lbrbc_status lbrbc_info(lbrbc_sim *sim, int64_t *out);
 
+/* ---- Batches of independent domains ------------------------------------
+ * Many domains of uneven size and their own parameters (same lattices and
+ * precision, 3D, no phase change) advanced together: each kernel phase of a
+ * step (fluid sweep, wet-boundary list, fluid-end gather) is ONE persistent
+ * launch over a schedule of work items from all domains, and step pairs are
+ * replayed from a CUDA graph.  Not a construct of the paper: a way to run
+ * many of its problems at once. */
+typedef struct lbrbc_batch lbrbc_batch; /* opaque, owned by the library */
+
+/* n domains: params[n] (host, copied), masks[n] (host pointers to nx*ny*nz
+ * bytes each), inits[n] or NULL.  Errors as lbrbc_create (message from
+ * lbrbc_batch_last_error(NULL)); phase_change must be 0. */
+lbrbc_status lbrbc_batch_create(int32_t n, const lbrbc_params *params, const uint8_t *const *masks,
+                                const lbrbc_init *inits, lbrbc_batch **out);
+
+/* Advance every domain by n steps (stream as in lbrbc_step). */
+lbrbc_status lbrbc_batch_step(lbrbc_batch *batch, int64_t n, void *stream);
+
+/* Autotuner: times each candidate schedule (tile width along x 128/64/32 or
+ * fitted to the domain, domain-major or largest-first interleaved order,
+ * 4/8/16 blocks per SM) for `pairs` step pairs plus one warm-up pair --
+ * real steps of every domain -- and keeps the fastest.  choice[3] (host,
+ * may be NULL) receives [tile policy, order, blocks per SM]; *ms_per_step
+ * (may be NULL) the best time per step in milliseconds. */
+lbrbc_status lbrbc_batch_autotune(lbrbc_batch *batch, int32_t pairs, void *stream, int64_t *choice,
+                                  double *ms_per_step);
+
+/* out[0] number of domains, out[1] total fluid cells (host, 2 entries). */
+lbrbc_status lbrbc_batch_info(lbrbc_batch *batch, int64_t *out);
+
+/* Handle of domain i for lbrbc_fields / lbrbc_mass_ledger / lbrbc_classes /
+ * lbrbc_check; owned by the batch (lbrbc_destroy ignores it, lbrbc_step on
+ * it fails).  NULL if i is out of range. */
+lbrbc_sim *lbrbc_batch_domain(lbrbc_batch *batch, int32_t i);
+
+const char *lbrbc_batch_last_error(lbrbc_batch *batch);
+void lbrbc_batch_destroy(lbrbc_batch *batch);
+
 /* Synchronise and report deferred device-side errors (non-finite state,
  * list overflow).  Returns LBRBC_OK, LBRBC_ERR_NUMERIC or LBRBC_ERR_STATE. */
 lbrbc_status lbrbc_check(lbrbc_sim *sim);

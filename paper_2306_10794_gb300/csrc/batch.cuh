@@ -1,0 +1,376 @@
+// Batched time stepping of many independent domains (uneven sizes, own
+// parameters) with one launch per kernel phase for the whole batch: the
+// fluid sweep, the wet-boundary list and the fluid-end gather each run as a
+// persistent kernel over a precomputed schedule of work items drawn from
+// every domain, and a pair of steps is replayed from one CUDA graph.  An
+// autotuner times candidate schedules (tile shape along x, tile order, grid
+// size) on the batch itself and keeps the fastest.
+#pragma once
+
+#include <algorithm>
+#include <memory>
+#include <numeric>
+#include <vector>
+
+#include "engine.cuh"
+
+namespace lbrbc {
+
+template <typename T>
+struct DomainDesc {
+    Dev<T> a;
+    Phys p;
+    PhysT<T> q;
+};
+
+// Fluid tile: 128 threads over tw cells along x times 128/tw rows along y at
+// one z.  x: domain, y: x0 | (log2(tw) << 24), z: y0, w: z.
+template <typename T, class LF, class LG, bool ODD>
+__global__ void __launch_bounds__(FLUID_BLOCK) kb_fluid(const DomainDesc<T>* __restrict__ dd, const int4* __restrict__ tiles,
+                                                     int ntiles) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int4 tl = tiles[t];
+        const DomainDesc<T>& D = dd[tl.x];
+        const int lw = tl.y >> 24;
+        const int tw = 1 << lw;
+        const int x = (tl.y & 0xffffff) + (threadIdx.x & (tw - 1));
+        const int y = tl.z + (threadIdx.x >> lw);
+        if (x < D.a.geo.nx && y < D.a.geo.ny) fluid_cell<T, LF, LG, ODD>(D.a, D.p, D.q, x, y, tl.w);
+    }
+}
+
+// Fluid-list chunk: FLUID_BLOCK consecutive entries of one domain's
+// compacted fluid-cell list.
+template <typename T, class LF, class LG, bool ODD>
+__global__ void __launch_bounds__(FLUID_BLOCK) kb_fluid_list4(const DomainDesc<T>* __restrict__ dd,
+                                                           const int4* __restrict__ chunks, int nchunks) {
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const int4 ch = chunks[c];
+        const DomainDesc<T>& D = dd[ch.x];
+        const int e = ch.y * FLUID_BLOCK + threadIdx.x;
+        if (e < *D.a.nfl) {
+            int x, y, z;
+            unpack32(D.a.fl_xyz[e], x, y, z);
+            fluid_cell<T, LF, LG, ODD>(D.a, D.p, D.q, x, y, z);
+        }
+    }
+}
+
+// Boundary chunk: LIST_BLOCK consecutive list entries of one domain; the
+// chunk's ledger partial goes to the domain's slot for that chunk.
+template <typename T, class LG, bool ODD>
+__global__ void __launch_bounds__(LIST_BLOCK) kb_bound(const DomainDesc<T>* __restrict__ dd, const int2* __restrict__ chunks,
+                                                    int nchunks) {
+    __shared__ __align__(16) unsigned char red_raw[2 * (LIST_BLOCK / 32) * sizeof(DiffSum<T>)];
+    DiffSum<T>* red = reinterpret_cast<DiffSum<T>*>(red_raw);
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const int2 ch = chunks[c];
+        const DomainDesc<T>& D = dd[ch.x];
+        const int e = ch.y * LIST_BLOCK + threadIdx.x;
+        DiffSum<T> racc, dacc;
+        if (e < *D.a.nb) bound_entry<T, LG, ODD>(D.a, D.p, D.q, e, racc, dacc);
+        racc = warp_merge(racc);
+        dacc = warp_merge(dacc);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) {
+            red[threadIdx.x >> 5] = racc;
+            red[LIST_BLOCK / 32 + (threadIdx.x >> 5)] = dacc;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            DiffSum<T> r = red[0], d = red[LIST_BLOCK / 32];
+            for (int k = 1; k < LIST_BLOCK / 32; ++k) {
+                r.merge(red[k]);
+                d.merge(red[LIST_BLOCK / 32 + k]);
+            }
+            if (r.sign() != 0 || d.sign() != 0) {
+                D.a.bacc[2 * ch.y] += r.value();
+                D.a.bacc[2 * ch.y + 1] += d.value();
+            }
+        }
+    }
+}
+
+template <typename T, class LG>
+__global__ void __launch_bounds__(LIST_BLOCK) kb_fend(const DomainDesc<T>* __restrict__ dd, const int2* __restrict__ chunks,
+                                                   int nchunks) {
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const int2 ch = chunks[c];
+        const DomainDesc<T>& D = dd[ch.x];
+        const int e = ch.y * LIST_BLOCK + threadIdx.x;
+        if (e < *D.a.nf) fend_entry<T, LG>(D.a, D.p, e);
+    }
+}
+
+#define LB_BCUDA(call)                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            err = std::string(#call) + ": " + cudaGetErrorString(e_);                     \
+            return 2;                                                                     \
+        }                                                                                 \
+    } while (0)
+
+template <typename T, class LF, class LG>
+class BatchEngine final : public IBatch {
+   public:
+    ~BatchEngine() override { release(); }
+
+    int init(int n, const lbrbc_params* P, const uint8_t* const* masks, const lbrbc_init* inits,
+             std::string& err) override {
+        (void)cudaGetLastError();
+        for (int i = 0; i < n; ++i) {
+            if (P[i].phase_change) {
+                err = "batched domains do not support phase change (domain " + std::to_string(i) + ")";
+                return 1;
+            }
+            auto* e = new Engine<T, LF, LG>();
+            e->set_batched();
+            e->force_list(true);
+            doms_.emplace_back(e);
+            const int rc = e->init(P[i], masks[i], inits ? &inits[i] : nullptr, err);
+            if (rc) {
+                err = "domain " + std::to_string(i) + ": " + err;
+                return rc;
+            }
+            if ((e->host_nb() + LIST_BLOCK - 1) / LIST_BLOCK > e->nbacc()) {
+                err = "domain " + std::to_string(i) + " has too many boundary cells for batching";
+                return 1;
+            }
+        }
+        std::vector<DomainDesc<T>> h(n);
+        for (int i = 0; i < n; ++i) {
+            h[i].a = doms_[i]->dev();
+            h[i].p = doms_[i]->phys();
+            h[i].q = doms_[i]->physt();
+        }
+        LB_BCUDA(cudaMalloc((void**)&dd_, sizeof(DomainDesc<T>) * n));
+        LB_BCUDA(cudaMemcpy(dd_, h.data(), sizeof(DomainDesc<T>) * n, cudaMemcpyHostToDevice));
+        // list chunks (fixed: no phase change)
+        std::vector<int2> bch, fch;
+        for (int i = 0; i < n; ++i) {
+            for (int c = 0; c * LIST_BLOCK < doms_[i]->host_nb(); ++c) bch.push_back(make_int2(i, c));
+            for (int c = 0; c * LIST_BLOCK < doms_[i]->host_nf(); ++c) fch.push_back(make_int2(i, c));
+        }
+        nbch_ = (int)bch.size();
+        nfch_ = (int)fch.size();
+        LB_BCUDA(cudaMalloc((void**)&bch_, sizeof(int2) * std::max(1, nbch_)));
+        LB_BCUDA(cudaMalloc((void**)&fch_, sizeof(int2) * std::max(1, nfch_)));
+        if (nbch_) LB_BCUDA(cudaMemcpy(bch_, bch.data(), sizeof(int2) * nbch_, cudaMemcpyHostToDevice));
+        if (nfch_) LB_BCUDA(cudaMemcpy(fch_, fch.data(), sizeof(int2) * nfch_, cudaMemcpyHostToDevice));
+        LB_BCUDA(cudaStreamCreateWithFlags(&own_, cudaStreamNonBlocking));
+        // default schedule until autotuned: fluid-list chunks, largest domains
+        // first, 8 blocks per SM
+        if (set_schedule(3, 1, 8, err)) return 2;
+        return 0;
+    }
+
+    int step(int64_t n, cudaStream_t s, std::string& err) override {
+        cudaStream_t st = s ? s : own_;
+        int64_t k = 0;
+        while (k < n) {
+            if (!lastodd_ || n - k < 2) {
+                LB_BCUDA(cudaGraphLaunch(lastodd_ ? g_even_ : g_odd_, st));
+                lastodd_ ^= 1;
+                k += 1;
+            } else {
+                LB_BCUDA(cudaGraphLaunch(g_pair_, st));
+                k += 2;
+            }
+        }
+        for (auto& d : doms_) d->advance(n, lastodd_, st);
+        if (!s) LB_BCUDA(cudaStreamSynchronize(own_));
+        return 0;
+    }
+
+    // Time each candidate schedule for `pairs` step pairs (real steps of every
+    // domain) and keep the fastest.  choice: [tile policy, order, blocks/SM].
+    int autotune(int pairs, cudaStream_t s, int64_t* choice, double* best_ms, std::string& err) override {
+        cudaStream_t st = s ? s : own_;
+        const int policies[] = {0, 1, 2, 3}, orders[] = {0, 1}, per_sm[] = {4, 8, 16};
+        double best = 1e30;
+        int bp = 0, bo = 1, bs = 8;
+        cudaEvent_t e0, e1;
+        LB_BCUDA(cudaEventCreate(&e0));
+        LB_BCUDA(cudaEventCreate(&e1));
+        for (int pol : policies)
+            for (int ord : orders)
+                for (int ps : per_sm) {
+                    if (set_schedule(pol, ord, ps, err)) return 2;
+                    if (step(2, st, err)) return 2;  // warm-up pair
+                    LB_BCUDA(cudaEventRecord(e0, st));
+                    if (step(2 * (int64_t)pairs, st, err)) return 2;
+                    LB_BCUDA(cudaEventRecord(e1, st));
+                    LB_BCUDA(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    LB_BCUDA(cudaEventElapsedTime(&ms, e0, e1));
+                    if (ms < best) {
+                        best = ms;
+                        bp = pol;
+                        bo = ord;
+                        bs = ps;
+                    }
+                }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (set_schedule(bp, bo, bs, err)) return 2;
+        if (choice) {
+            choice[0] = bp;
+            choice[1] = bo;
+            choice[2] = bs;
+        }
+        if (best_ms) *best_ms = best / (2.0 * pairs);
+        return 0;
+    }
+
+    int size() const override { return (int)doms_.size(); }
+    ISim* domain(int i) override { return doms_[i].get(); }
+    long long fluid_cells() const override {
+        long long s = 0;
+        for (auto& d : doms_) s += d->fluid_cells();
+        return s;
+    }
+
+   private:
+    // Tile policy 0: width min(128, pow2 >= nx); 1: 64; 2: 32; 3: chunks of
+    // each domain's compacted fluid-cell list instead of dense tiles.  Order
+    // 0: domain by domain; 1: largest domains first with the work items of
+    // all domains interleaved round-robin.
+    int set_schedule(int policy, int order, int per_sm, std::string& err) {
+        policy_ = policy;
+        std::vector<std::vector<int4>> per(doms_.size());
+        for (size_t i = 0; i < doms_.size() && policy == 3; ++i)
+            for (int c = 0; c * FLUID_BLOCK < doms_[i]->host_nfl(); ++c) per[i].push_back(make_int4((int)i, c, 0, 0));
+        for (size_t i = 0; i < doms_.size() && policy != 3; ++i) {
+            const Geo& g = doms_[i]->geo();
+            int tw = 128;
+            if (policy == 0)
+                while (tw > 32 && tw / 2 >= g.nx) tw /= 2;
+            else tw = policy == 1 ? 64 : 32;
+            int lw = 0;
+            while ((1 << lw) < tw) ++lw;
+            const int rows = FLUID_BLOCK / tw;
+            for (int z = 0; z < g.nz; ++z)
+                for (int y0 = 0; y0 < g.ny; y0 += rows)
+                    for (int x0 = 0; x0 < g.nx; x0 += tw) per[i].push_back(make_int4((int)i, x0 | (lw << 24), y0, z));
+        }
+        std::vector<int4> tiles;
+        if (order == 0) {
+            for (auto& v : per) tiles.insert(tiles.end(), v.begin(), v.end());
+        } else {
+            std::vector<size_t> idx(per.size());
+            std::iota(idx.begin(), idx.end(), 0);
+            std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return per[a].size() > per[b].size(); });
+            size_t k = 0;
+            bool more = true;
+            while (more) {
+                more = false;
+                for (size_t i : idx)
+                    if (k < per[i].size()) {
+                        tiles.push_back(per[i][k]);
+                        more = true;
+                    }
+                ++k;
+            }
+        }
+        ntiles_ = (int)tiles.size();
+        if (tiles_) cudaFree(tiles_);
+        tiles_ = nullptr;
+        LB_BCUDA(cudaMalloc((void**)&tiles_, sizeof(int4) * std::max(1, ntiles_)));
+        LB_BCUDA(cudaMemcpy(tiles_, tiles.data(), sizeof(int4) * ntiles_, cudaMemcpyHostToDevice));
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        grid_ = std::max(1, nsm * per_sm);
+        return build_graphs(err);
+    }
+
+    int enqueue(cudaStream_t st, bool odd, std::string& err) {
+        const int gf = std::min(grid_, std::max(1, ntiles_));
+        const int gb = std::min(grid_, std::max(1, nbch_));
+        const int ge = std::min(grid_, std::max(1, nfch_));
+        if (policy_ == 3) {
+            // list chunks are stored in the tile array as {domain, chunk, 0, 0}
+            if (odd) kb_fluid_list4<T, LF, LG, true><<<gf, FLUID_BLOCK, 0, st>>>(dd_, tiles_, ntiles_);
+            else kb_fluid_list4<T, LF, LG, false><<<gf, FLUID_BLOCK, 0, st>>>(dd_, tiles_, ntiles_);
+        } else {
+            if (odd) kb_fluid<T, LF, LG, true><<<gf, FLUID_BLOCK, 0, st>>>(dd_, tiles_, ntiles_);
+            else kb_fluid<T, LF, LG, false><<<gf, FLUID_BLOCK, 0, st>>>(dd_, tiles_, ntiles_);
+        }
+        if (nbch_) {
+            if (odd) kb_bound<T, LG, true><<<gb, LIST_BLOCK, 0, st>>>(dd_, bch_, nbch_);
+            else kb_bound<T, LG, false><<<gb, LIST_BLOCK, 0, st>>>(dd_, bch_, nbch_);
+        }
+        if (nfch_) kb_fend<T, LG><<<ge, LIST_BLOCK, 0, st>>>(dd_, fch_, nfch_);
+        LB_BCUDA(cudaGetLastError());
+        return 0;
+    }
+
+    int build_graphs(std::string& err) {
+        drop_graphs();
+        cudaStream_t cs;
+        LB_BCUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        auto cap = [&](cudaGraphExec_t* out, int mode) -> int {
+            cudaGraph_t gr;
+            LB_BCUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            int r = 0;
+            if (mode == 0) r = enqueue(cs, false, err);
+            else if (mode == 1) r = enqueue(cs, true, err);
+            else {
+                r = enqueue(cs, false, err);
+                if (!r) r = enqueue(cs, true, err);
+            }
+            cudaError_t e = cudaStreamEndCapture(cs, &gr);
+            if (r) return r;
+            if (e != cudaSuccess) {
+                err = std::string("graph capture: ") + cudaGetErrorString(e);
+                return 2;
+            }
+            LB_BCUDA(cudaGraphInstantiate(out, gr, 0));
+            cudaGraphDestroy(gr);
+            return 0;
+        };
+        const int r = cap(&g_even_, 0) || cap(&g_odd_, 1) || cap(&g_pair_, 2);
+        cudaStreamDestroy(cs);
+        if (r) return 2;
+        graphs_ = true;
+        return 0;
+    }
+
+    void drop_graphs() {
+        if (!graphs_) return;
+        cudaGraphExecDestroy(g_even_);
+        cudaGraphExecDestroy(g_odd_);
+        cudaGraphExecDestroy(g_pair_);
+        graphs_ = false;
+    }
+
+    void release() {
+        if (own_) cudaStreamSynchronize(own_);
+        drop_graphs();
+        if (dd_) cudaFree(dd_);
+        if (tiles_) cudaFree(tiles_);
+        if (bch_) cudaFree(bch_);
+        if (fch_) cudaFree(fch_);
+        dd_ = nullptr;
+        tiles_ = nullptr;
+        bch_ = fch_ = nullptr;
+        doms_.clear();
+        if (own_) cudaStreamDestroy(own_);
+        own_ = nullptr;
+    }
+
+    std::vector<std::unique_ptr<Engine<T, LF, LG>>> doms_;
+    DomainDesc<T>* dd_ = nullptr;
+    int4* tiles_ = nullptr;
+    int2 *bch_ = nullptr, *fch_ = nullptr;
+    int ntiles_ = 0, nbch_ = 0, nfch_ = 0, grid_ = 0, policy_ = 0;
+    int lastodd_ = 1;
+    cudaStream_t own_ = nullptr;
+    cudaGraphExec_t g_even_{}, g_odd_{}, g_pair_{};
+    bool graphs_ = false;
+};
+
+#undef LB_BCUDA
+
+}  // namespace lbrbc

@@ -25,6 +25,7 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -162,13 +163,19 @@ struct Dev {
     uint64_t* b_xyz;      // packed cell coordinates (21 bits each)
     T* b_kappa;           // (QG-1) * cap_b
     double* b_krate;      // cap_b or null
-    T* b_share;           // (QG-1) * cap_b, precipitation shares (storage precision)
+    int* b_fslot;         // (QG-1) * cap_b: slot in f_share of the fluid end of link o, or -1
     int* bmap;            // NP
     // fluid cells receiving precipitation shares
     int cap_f;
     int* nf;
     int* f_idx;
-    int* f_src;           // (QG-1) * cap_f, entry of the boundary cell at x - e_o
+    T* f_share;           // (QG-1) * cap_f: share received from the boundary cell at x - e_o
+    // compacted fluid cells (packed x | y << 11 | z << 22), when the sweep
+    // runs over a list instead of the dense grid
+    int use_fl;
+    int cap_fl;
+    int* nfl;
+    uint32_t* fl_xyz;
     // phase-change events of the current step
     int cap_e;
     int* nev;
@@ -331,13 +338,12 @@ __device__ __forceinline__ void st_pop(T* p, T v) {
 #endif
 }
 
+// One fluid cell (x, y, z) of one step; shared by the single-domain and the
+// batched sweeps.
 template <typename T, class LF, class LG, bool ODD>
-__global__ void __launch_bounds__(FLUID_BLOCK) k_fluid(const Dev<T> a, const Phys p, const PhysT<T> q) {
+__device__ __forceinline__ void fluid_cell(const Dev<T>& a, const Phys& p, const PhysT<T>& q, int x, int y, int z) {
     constexpr int QF = LF::Q, QG = LG::Q;
     const Geo& g = a.geo;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
-    if (x >= g.nx) return;
     const uint32_t id = (uint32_t)g.idx(x, y, z);
     const uint32_t w = a.nw[id];
     if ((w & 3u) != CLS_FLUID) return;
@@ -437,6 +443,31 @@ __global__ void __launch_bounds__(FLUID_BLOCK) k_fluid(const Dev<T> a, const Phy
     }
 }
 
+template <typename T, class LF, class LG, bool ODD>
+__global__ void __launch_bounds__(FLUID_BLOCK) k_fluid(const Dev<T> a, const Phys p, const PhysT<T> q) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= a.geo.nx) return;
+    fluid_cell<T, LF, LG, ODD>(a, p, q, x, blockIdx.y, blockIdx.z);
+}
+
+// The same sweep over the compacted fluid cells: every lane of a warp has a
+// fluid cell, which pays off in porous media where most 32-cell row
+// segments of the dense grid are partly solid.
+__device__ __forceinline__ void unpack32(uint32_t v, int& x, int& y, int& z) {
+    x = (int)(v & 2047u);
+    y = (int)((v >> 11) & 2047u);
+    z = (int)(v >> 22);
+}
+
+template <typename T, class LF, class LG, bool ODD>
+__global__ void __launch_bounds__(FLUID_BLOCK) k_fluid_list(const Dev<T> a, const Phys p, const PhysT<T> q) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= *a.nfl) return;
+    int x, y, z;
+    unpack32(a.fl_xyz[e], x, y, z);
+    fluid_cell<T, LF, LG, ODD>(a, p, q, x, y, z);
+}
+
 // ---------------------------------------------------------------------------
 // Event queue with warp-aggregated atomics.
 // ---------------------------------------------------------------------------
@@ -472,7 +503,11 @@ template <typename T>
 struct DiffSum {
     double s = 0.0;
     __device__ __forceinline__ void add(double a, double b) { s += a - b; }
+    __device__ __forceinline__ void merge(const DiffSum& o) { s += o.s; }
     __device__ __forceinline__ double value() const { return s; }
+    __device__ __forceinline__ int sign() const { return s > 0.0 ? 1 : (s < 0.0 ? -1 : 0); }
+    __device__ __forceinline__ double approx() const { return s; }
+    __device__ __forceinline__ void shfl_down(int off) { s = __shfl_down_sync(0xffffffffu, s, off); }
 };
 template <>
 struct DiffSum<float> {
@@ -488,8 +523,36 @@ struct DiffSum<float> {
         hi = s2 + tl;
         lo = tl - (hi - s2);
     }
+    __device__ __forceinline__ void merge(const DiffSum& o) {
+        const float s2 = hi + o.hi;
+        const float bb = s2 - hi;
+        const float t = (hi - (s2 - bb)) + (o.hi - bb);
+        const float tl = t + (lo + o.lo);
+        hi = s2 + tl;
+        lo = tl - (hi - s2);
+    }
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+    __device__ __forceinline__ int sign() const {
+        const float v = hi != 0.f ? hi : lo;
+        return v > 0.f ? 1 : (v < 0.f ? -1 : 0);
+    }
+    __device__ __forceinline__ float approx() const { return hi + lo; }
+    __device__ __forceinline__ void shfl_down(int off) {
+        hi = __shfl_down_sync(0xffffffffu, hi, off);
+        lo = __shfl_down_sync(0xffffffffu, lo, off);
+    }
 };
+
+template <typename T>
+__device__ __forceinline__ DiffSum<T> warp_merge(DiffSum<T> v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        DiffSum<T> w = v;
+        w.shfl_down(o);
+        v.merge(w);
+    }
+    return v;
+}
 
 // phi <= 0 and phi >= 1 on the bit pattern of a (non-NaN) double: integer
 // compares, no FP64 instruction.
@@ -514,140 +577,147 @@ __device__ __forceinline__ void unpack_xyz(uint64_t v, int& x, int& y, int& z) {
     z = (int)((v >> 42) & 0x1fffffu);
 }
 
+// One wet boundary cell (list entry e) of one step; adds its reacted mass
+// (or Dirichlet inflow) to racc (dacc).
 template <typename T, class LG, bool ODD>
-__global__ void __launch_bounds__(LIST_BLOCK) k_bound(const Dev<T> a, const Phys p, const PhysT<T> q) {
+__device__ __forceinline__ void bound_entry(const Dev<T>& a, const Phys& p, const PhysT<T>& q, int e, DiffSum<T>& racc,
+                                            DiffSum<T>& dacc) {
     constexpr int Q = LG::Q;
     const Geo& g = a.geo;
     const uint32_t NP = (uint32_t)g.NP;
     T* __restrict__ G = a.G;
-    const int n = *a.nb;
-    double rsum = 0.0, dsum = 0.0;
     const T cref = q.cref;
     const T gam = q.gamma, ics2 = q.ics2;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-        int x, y, z;
-        unpack_xyz(a.b_xyz[e], x, y, z);
-        const uint32_t b = (uint32_t)g.idx(x, y, z);
-        const Nbr32 d = nbr32(g, x, y, z);
-        const uint32_t bw = a.b_word[e];
-        T gp[Q];
+    int x, y, z;
+    unpack_xyz(a.b_xyz[e], x, y, z);
+    const uint32_t b = (uint32_t)g.idx(x, y, z);
+    const Nbr32 d = nbr32(g, x, y, z);
+    const uint32_t bw = a.b_word[e];
+    T gp[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const bool inactive = i > 0 && ((bw >> (i - 1)) & 1u);
-            gp[i] = G[read_slot<LG, ODD>(b, d, NP, i, inactive)];
-        }
-        T gq[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) gq[i] = gp[i];
-        const bool dir = (bw & BW_DIRICHLET) != 0u;
-        const T kr = a.b_krate ? T(a.b_krate[e]) : q.k_r;
-        T mabs[Q];
-        DiffSum<T> ms;
-        T S = T(0);
-#pragma unroll
-        for (int o = 1; o < Q; ++o) {
-            mabs[o] = T(0);
-            if (!((bw >> (BW_LINK + o - 1)) & 1u)) continue;
-            const T gt = gp[LG::opp(o)];
-            const T w2 = T(2) * q.gw[o];
-            T val;
-            if (dir) {
-                val = -gt + w2 * q.c_dir_d;  // anti-bounce-back, C_wall = c_dirichlet
-            } else {
-                const T kap = a.b_kappa[(long long)(o - 1) * a.cap_b + e];
-                T k = T(0);
-                bool inf = false;
-                if (p.scheme == 0) k = gam * kr * kap * ics2;
-                else if (p.scheme == 1) k = kr * kap * ics2;
-                else if (p.scheme == 2) {
-                    if (kap > T(0)) k = gam * kr * ics2 / kap;
-                    else inf = true;
-                } else inf = true;
-                if (inf) val = -gt + w2 * q.c_eq_d;
-                else {
-                    const T ik = T(1) / (T(1) + k);
-                    val = k * ik * w2 * q.c_eq_d + (T(1) - k) * ik * gt;
-                }
-            }
-            ms.add(val, gp[o]);
-            mabs[o] = fabs(val - gp[o]);
-            S += mabs[o];
-            gq[o] = val;
-        }
-        T sc = T(0);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) sc += gq[i];
-        const T C = cref + sc;
-        if (!isfinite(C)) *a.err |= ERR_NUMERIC;
-        collide_solute<LG, T>(gq, C, T(0), T(0), T(0), p, q);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) G[write_slot<LG, ODD>(b, d, NP, i)] = gq[i];
-        const double M = ms.value();
-        T* sh = a.b_share + e;
-        if (dir) {
-            dsum += M;
-#pragma unroll
-            for (int o = 1; o < Q; ++o) sh[(long long)(o - 1) * a.cap_b] = T(0);
-            continue;
-        }
-        rsum += M;
-        const bool diss = __double_as_longlong(M) > 0LL;   // M > 0
-        const bool prec = __double_as_longlong(M) < 0LL && (__double_as_longlong(M) << 1) != 0LL;  // M < 0
-        double ph = 0.0;
-        if (diss || p.phase_change) ph = a.phi[b];
-        if (diss) {
-            ph -= p.Vm * M;
-            a.phi[b] = ph;
-        }
-        const T r = (prec && S > T(0)) ? q.neg_vm * T(M) / S : T(0);
-#pragma unroll
-        for (int o = 1; o < Q; ++o) sh[(long long)(o - 1) * a.cap_b] = r * mabs[o];
-        if (p.phase_change && dle0(ph)) push_event(a.nev, a.cap_e, a.ev_node, a.ev_kind, a.err, (int)b, EV_DISSOLVE);
+    for (int i = 0; i < Q; ++i) {
+        const bool inactive = i > 0 && ((bw >> (i - 1)) & 1u);
+        gp[i] = G[read_slot<LG, ODD>(b, d, NP, i, inactive)];
     }
+    T gq[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) gq[i] = gp[i];
+    const bool dir = (bw & BW_DIRICHLET) != 0u;
+    const T kr = a.b_krate ? T(a.b_krate[e]) : q.k_r;
+    T mabs[Q];
+    DiffSum<T> ms;
+    T S = T(0);
+#pragma unroll
+    for (int o = 1; o < Q; ++o) {
+        mabs[o] = T(0);
+        if (!((bw >> (BW_LINK + o - 1)) & 1u)) continue;
+        const T gt = gp[LG::opp(o)];
+        const T w2 = T(2) * q.gw[o];
+        T val;
+        if (dir) {
+            val = -gt + w2 * q.c_dir_d;  // anti-bounce-back, C_wall = c_dirichlet
+        } else {
+            const T kap = a.b_kappa[(long long)(o - 1) * a.cap_b + e];
+            T k = T(0);
+            bool inf = false;
+            if (p.scheme == 0) k = gam * kr * kap * ics2;
+            else if (p.scheme == 1) k = kr * kap * ics2;
+            else if (p.scheme == 2) {
+                if (kap > T(0)) k = gam * kr * ics2 / kap;
+                else inf = true;
+            } else inf = true;
+            if (inf) val = -gt + w2 * q.c_eq_d;
+            else {
+                const T ik = T(1) / (T(1) + k);
+                val = k * ik * w2 * q.c_eq_d + (T(1) - k) * ik * gt;
+            }
+        }
+        ms.add(val, gp[o]);
+        mabs[o] = fabs(val - gp[o]);
+        S += mabs[o];
+        gq[o] = val;
+    }
+    T sc = T(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) sc += gq[i];
+    const T C = cref + sc;
+    if (!isfinite(C)) *a.err |= ERR_NUMERIC;
+    collide_solute<LG, T>(gq, C, T(0), T(0), T(0), p, q);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) G[write_slot<LG, ODD>(b, d, NP, i)] = gq[i];
+    const int sg = ms.sign();
+    if (dir) {
+        dacc.merge(ms);
+        return;
+    }
+    racc.merge(ms);
+    double ph = 0.0;
+    if (sg > 0 || p.phase_change) ph = a.phi[b];
+    if (sg > 0) {  // dissolution: the boundary cell loses solid (the only FP64 arithmetic here)
+        ph -= p.Vm * ms.value();
+        a.phi[b] = ph;
+    }
+    const T r = (sg < 0 && S > T(0)) ? q.neg_vm * T(ms.approx()) / S : T(0);
+#pragma unroll
+    for (int o = 1; o < Q; ++o) {
+        const int slot = a.b_fslot[(long long)(o - 1) * a.cap_b + e];
+        if (slot >= 0) a.f_share[slot] = r * mabs[o];
+    }
+    if (p.phase_change && dle0(ph)) push_event(a.nev, a.cap_e, a.ev_node, a.ev_kind, a.err, (int)b, EV_DISSOLVE);
+}
+
+template <typename T, class LG, bool ODD>
+__global__ void __launch_bounds__(LIST_BLOCK) k_bound(const Dev<T> a, const Phys p, const PhysT<T> q) {
+    const int n = *a.nb;
+    DiffSum<T> racc, dacc;  // reacted mass and Dirichlet inflow of this thread
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
+        bound_entry<T, LG, ODD>(a, p, q, e, racc, dacc);
     // each block owns its two accumulators (fixed grid): no atomics and a
     // fixed summation order
-    __shared__ double red[2][LIST_BLOCK / 32];
-    rsum = warp_sum(rsum);
-    dsum = warp_sum(dsum);
+    __shared__ __align__(16) unsigned char red_raw[2 * (LIST_BLOCK / 32) * sizeof(DiffSum<T>)];
+    DiffSum<T>* red = reinterpret_cast<DiffSum<T>*>(red_raw);  // [2][LIST_BLOCK / 32]
+    racc = warp_merge(racc);
+    dacc = warp_merge(dacc);
     if ((threadIdx.x & 31) == 0) {
-        red[0][threadIdx.x >> 5] = rsum;
-        red[1][threadIdx.x >> 5] = dsum;
+        red[threadIdx.x >> 5] = racc;
+        red[LIST_BLOCK / 32 + (threadIdx.x >> 5)] = dacc;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double r = 0.0, q = 0.0;
-        for (int k = 0; k < LIST_BLOCK / 32; ++k) {
-            r += red[0][k];
-            q += red[1][k];
+        DiffSum<T> r = red[0], d = red[LIST_BLOCK / 32];
+        for (int k = 1; k < LIST_BLOCK / 32; ++k) {
+            r.merge(red[k]);
+            d.merge(red[LIST_BLOCK / 32 + k]);
         }
-        if (r != 0.0 || q != 0.0) {
-            a.bacc[2 * blockIdx.x] += r;
-            a.bacc[2 * blockIdx.x + 1] += q;
+        if (r.sign() != 0 || d.sign() != 0) {
+            a.bacc[2 * blockIdx.x] += r.value();
+            a.bacc[2 * blockIdx.x + 1] += d.value();
         }
     }
 }
 
 // Fluid cells at the ends of reactive links gather their precipitation
 // shares (fixed direction order) and test the phi >= 1 threshold.
+// One fluid cell at the end of reactive links (list entry e): gathers its
+// precipitation shares in fixed direction order and tests phi >= 1.
+template <typename T, class LG>
+__device__ __forceinline__ void fend_entry(const Dev<T>& a, const Phys& p, int e) {
+    const long long f = a.f_idx[e];
+    T acc = T(0);
+#pragma unroll
+    for (int o = 1; o < LG::Q; ++o) acc += a.f_share[(long long)(o - 1) * a.cap_f + e];
+    double ph = a.phi[f];
+    if (acc != T(0)) {
+        ph += (double)acc;
+        a.phi[f] = ph;
+    }
+    if (p.phase_change && dge1(ph)) push_event(a.nev, a.cap_e, a.ev_node, a.ev_kind, a.err, (int)f, EV_PRECIPITATE);
+}
+
 template <typename T, class LG>
 __global__ void __launch_bounds__(LIST_BLOCK) k_fend(const Dev<T> a, const Phys p) {
     const int n = *a.nf;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-        const long long f = a.f_idx[e];
-        T acc = T(0);
-#pragma unroll
-        for (int o = 1; o < LG::Q; ++o) {
-            const int s = a.f_src[(long long)(o - 1) * a.cap_f + e];
-            if (s >= 0) acc += a.b_share[(long long)(o - 1) * a.cap_b + s];
-        }
-        double ph = a.phi[f];
-        if (acc != T(0)) {
-            ph += (double)acc;
-            a.phi[f] = ph;
-        }
-        if (p.phase_change && dge1(ph))
-            push_event(a.nev, a.cap_e, a.ev_node, a.ev_kind, a.err, (int)f, EV_PRECIPITATE);
-    }
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) fend_entry<T, LG>(a, p, e);
 }
 
 // ---------------------------------------------------------------------------
@@ -982,6 +1052,7 @@ __global__ void k_count(const Dev<T> a, int which, int force) {
         const long long id = g.idx(x, y, z);
         const uint32_t cls = a.nw[id] & 3u;
         if (which == 0) local += cls == CLS_BOUND;
+        else if (which == 2) local += cls == CLS_FLUID;
         else if (cls == CLS_FLUID) {
 #pragma unroll
             for (int o = 1; o < LG::Q; ++o) {
@@ -1018,9 +1089,9 @@ __global__ void k_scan(const Dev<T> a, int nchunks, int which, int force) {
             part[k] = run;
             run += v;
         }
-        const int cap = which == 0 ? a.cap_b : a.cap_f;
+        const int cap = which == 0 ? a.cap_b : (which == 1 ? a.cap_f : a.cap_fl);
         if (run > cap) atomicOr(a.err, ERR_OVERFLOW);
-        *(which == 0 ? a.nb : a.nf) = min(run, cap);
+        *(which == 0 ? a.nb : (which == 1 ? a.nf : a.nfl)) = min(run, cap);
     }
     __syncthreads();
     int run = part[threadIdx.x];
@@ -1058,6 +1129,8 @@ __global__ void k_write_lists(const Dev<T> a, const Phys p, int which, int force
             if (which == 0) {
                 sel = cls == CLS_BOUND;
                 a.bmap[id] = -1;
+            } else if (which == 2) {
+                sel = cls == CLS_FLUID;
             } else if (cls == CLS_FLUID) {
 #pragma unroll
                 for (int o = 1; o < LG::Q; ++o) {
@@ -1110,10 +1183,18 @@ __global__ void k_write_lists(const Dev<T> a, const Phys p, int which, int force
                 }
                 a.b_word[pos] = bw;
                 if (a.b_krate) a.b_krate[pos] = a.kfield ? a.kfield[id] : p.k_r;
+#pragma unroll
+                for (int o = 1; o < LG::Q; ++o) a.b_fslot[(long long)(o - 1) * a.cap_b + pos] = -1;
+            } else if (which == 2 && pos < a.cap_fl) {
+                a.fl_xyz[pos] = (uint32_t)x | ((uint32_t)y << 11) | ((uint32_t)z << 22);
             } else if (which == 1 && pos < a.cap_f) {
                 a.f_idx[pos] = (int)id;
 #pragma unroll
-                for (int o = 1; o < LG::Q; ++o) a.f_src[(long long)(o - 1) * a.cap_f + pos] = src[o];
+                for (int o = 1; o < LG::Q; ++o) {
+                    const long long slot = (long long)(o - 1) * a.cap_f + pos;
+                    a.f_share[slot] = T(0);
+                    if (src[o] >= 0) a.b_fslot[(long long)(o - 1) * a.cap_b + src[o]] = (int)slot;
+                }
             }
         }
         __syncthreads();
@@ -1438,6 +1519,7 @@ class Engine final : public ISim {
         long long nb0 = 0, nf0 = 0;
         count_lists_host(kind, nb0, nf0);
         nb0_ = nb0;
+        nf0_ = nf0;
         auto grow = [&](long long n0) {
             long long c = std::max<long long>(4 * n0, n0 + ncell_ / 16) + 1024;
             return (int)std::min<long long>(c, ncell_ + 1024);
@@ -1445,6 +1527,30 @@ class Engine final : public ISim {
         d_.cap_b = grow(nb0);
         d_.cap_f = grow(nf0);
         d_.cap_e = (int)std::min<long long>(ncell_ + 64, std::max<long long>(1 << 16, ncell_ / 64));
+        // Sweep over the dense grid (default) or over a compacted fluid-cell
+        // list (LBRBC_FLUID_SWEEP=list, or a batch schedule).  Measured on
+        // GB300 sphere packs the list is slower: a warp's 32 list cells span
+        // several rows, so every population load touches more lines.
+        {
+            long long active = 0;
+            for (int z = 0; z < g.nz; ++z)
+                for (int y = 0; y < g.ny; ++y)
+                    for (int x0 = 0; x0 < g.nx; x0 += 32) {
+                        bool any = false;
+                        for (int x = x0; x < std::min(g.nx, x0 + 32) && !any; ++x)
+                            any = mask[x + (long long)g.nx * (y + (long long)g.ny * z)] == KIND_FLUID;
+                        active += any;
+                    }
+            lane_eff_ = active ? (double)nfluid / (32.0 * active) : 1.0;
+            const bool fits = g.nx <= 2048 && g.ny <= 2048 && g.nz <= 1024;
+            const char* env = getenv("LBRBC_FLUID_SWEEP");
+            int want = 0;
+            if (env && !strcmp(env, "list")) want = 1;
+            if (env && !strcmp(env, "dense")) want = 0;
+            if (force_list_) want = 1;
+            d_.use_fl = want && fits;
+            d_.cap_fl = (int)std::min<long long>(ncell_, std::max<long long>(2 * nfluid, nfluid + ncell_ / 8) + 1024);
+        }
         d_.cap_log = P.event_log_capacity > 0 ? P.event_log_capacity : 0;
         nchunks_ = (int)((ncell_ + SCAN_CHUNK - 1) / SCAN_CHUNK);
 
@@ -1463,11 +1569,15 @@ class Engine final : public ISim {
         LB_CUDA(dalloc(&d_.b_word, (size_t)d_.cap_b));
         LB_CUDA(dalloc(&d_.b_xyz, (size_t)d_.cap_b));
         LB_CUDA(dalloc(&d_.b_kappa, (size_t)(QG - 1) * d_.cap_b));
-        LB_CUDA(dalloc(&d_.b_share, (size_t)(QG - 1) * d_.cap_b));
+        LB_CUDA(dalloc(&d_.b_fslot, (size_t)(QG - 1) * d_.cap_b));
         LB_CUDA(dalloc(&d_.bmap, (size_t)NP));
         LB_CUDA(dalloc(&d_.nf, 1));
         LB_CUDA(dalloc(&d_.f_idx, (size_t)d_.cap_f));
-        LB_CUDA(dalloc(&d_.f_src, (size_t)(QG - 1) * d_.cap_f));
+        LB_CUDA(dalloc(&d_.f_share, (size_t)(QG - 1) * d_.cap_f));
+        LB_CUDA(dalloc(&d_.nfl, 1));
+        if (d_.use_fl) LB_CUDA(dalloc(&d_.fl_xyz, (size_t)d_.cap_fl));
+        else d_.fl_xyz = nullptr;
+        LB_CUDA(cudaMemset(d_.nfl, 0, sizeof(int)));
         LB_CUDA(dalloc(&d_.nev, 1));
         LB_CUDA(dalloc(&d_.ev_node, (size_t)d_.cap_e));
         LB_CUDA(dalloc(&d_.ev_kind, (size_t)d_.cap_e));
@@ -1574,6 +1684,10 @@ class Engine final : public ISim {
     }
 
     int step(int64_t n, cudaStream_t s, std::string& err) override {
+        if (batched_) {
+            err = "this domain belongs to a batch: step it with lbrbc_batch_step";
+            return 5;
+        }
         cudaStream_t st = s ? s : own_;
         int64_t k = 0;
         // the state's parity decides which graph comes first
@@ -1748,6 +1862,24 @@ class Engine final : public ISim {
         return 0;
     }
 
+    // Accessors used by the batched engine.
+    const PhysT<T>& physt() const { return pt_; }
+    int nbacc() const { return nbacc_; }
+    const Geo& geo() const { return d_.geo; }
+    int host_nb() const { return (int)nb0_; }
+    int host_nf() const { return (int)nf0_; }
+    void set_batched() { batched_ = true; }
+    void force_list(bool v) { force_list_ = v; }
+    bool uses_list() const { return d_.use_fl != 0; }
+    double lane_efficiency() const { return lane_eff_; }
+    int host_nfl() const { return (int)nfluid_; }
+    // Record n steps taken by the batched kernels (parity after them: lastodd).
+    void advance(int64_t n, int lastodd, cudaStream_t st) {
+        steps_ += n;
+        lastodd_ = lastodd;
+        last_stream_ = st;
+    }
+
     long long fluid_cells() const override { return nfluid_; }
     long long boundary_cells() const override { return nb0_; }
     int red_blocks() const { return (int)std::min<long long>(1024, (ncell_ + RED_BLOCK - 1) / RED_BLOCK); }
@@ -1824,7 +1956,7 @@ class Engine final : public ISim {
     // Reclassification and list rebuild (force = 1 at creation: unconditional).
     int rebuild(cudaStream_t st, int lastodd, int force, std::string& err) {
         k_reclassify<T, LF, LG><<<grid_for(ncell_, 256), 256, 0, st>>>(d_, ph_, lastodd, force);
-        for (int which = 0; which < 2; ++which) {
+        for (int which = 0; which < (d_.use_fl ? 3 : 2); ++which) {
             k_count<T, LG><<<nchunks_, 256, 0, st>>>(d_, which, force);
             k_scan<T><<<1, 1024, 0, st>>>(d_, nchunks_, which, force);
             k_write_lists<T, LG><<<nchunks_, 256, 0, st>>>(d_, ph_, which, force);
@@ -1839,8 +1971,14 @@ class Engine final : public ISim {
         const Geo& g = d_.geo;
         dim3 grid((g.nx + FLUID_BLOCK - 1) / FLUID_BLOCK, g.ny, g.nz);
         if (ev) LB_CUDA(cudaEventRecord(ev[0], st));
-        if (odd) k_fluid<T, LF, LG, true><<<grid, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_);
-        else k_fluid<T, LF, LG, false><<<grid, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_);
+        if (d_.use_fl) {
+            const int gl = (int)((d_.cap_fl + FLUID_BLOCK - 1) / FLUID_BLOCK);
+            if (odd) k_fluid_list<T, LF, LG, true><<<gl, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_);
+            else k_fluid_list<T, LF, LG, false><<<gl, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_);
+        } else {
+            if (odd) k_fluid<T, LF, LG, true><<<grid, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_);
+            else k_fluid<T, LF, LG, false><<<grid, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_);
+        }
         if (ev) LB_CUDA(cudaEventRecord(ev[1], st));
         const int lg = list_grid(d_.cap_b);
         if (odd) k_bound<T, LG, true><<<lg, LIST_BLOCK, 0, st>>>(d_, ph_, pt_);
@@ -1950,7 +2088,7 @@ class Engine final : public ISim {
     Dev<T> d_{};
     Phys ph_{};
     PhysT<T> pt_{};
-    long long ncell_ = 0, nfluid_ = 0, nb0_ = 0;
+    long long ncell_ = 0, nfluid_ = 0, nb0_ = 0, nf0_ = 0;
     int nchunks_ = 0;
     int nbacc_ = 0;
     int lastodd_ = 1;
@@ -1958,6 +2096,9 @@ class Engine final : public ISim {
     cudaStream_t own_ = nullptr, last_stream_ = nullptr;
     cudaGraphExec_t g_even_{}, g_odd_{}, g_pair_{};
     bool graphs_ = false;
+    bool batched_ = false;
+    bool force_list_ = false;
+    double lane_eff_ = 1.0;
     std::vector<void*> allocs_;
 };
 

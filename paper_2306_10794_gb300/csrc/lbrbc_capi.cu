@@ -6,14 +6,10 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "sim_iface.h"
 
-struct lbrbc_sim {
-    lbrbc::ISim* impl = nullptr;
-    std::string err;
-    int device = 0;
-};
 
 namespace {
 
@@ -25,7 +21,17 @@ lbrbc_status fail(lbrbc_sim* s, int code, const std::string& msg) {
     return (lbrbc_status)code;
 }
 
-std::string validate(const lbrbc_params& p) {
+}  // namespace
+
+std::string lbrbc_validate_params(const lbrbc_params& p);
+
+namespace {
+
+std::string validate(const lbrbc_params& p) { return lbrbc_validate_params(p); }
+
+}  // namespace
+
+std::string lbrbc_validate_params(const lbrbc_params& p) {
     if (p.dim != 2 && p.dim != 3) return "dim must be 2 or 3";
     if (p.nx < 1 || p.ny < 1 || (p.dim == 3 && p.nz < 1)) return "grid sizes must be positive";
     if (p.dim == 2 && p.nz != 1 && p.nz != 0) return "2D grids need nz = 1";
@@ -52,8 +58,6 @@ std::string validate(const lbrbc_params& p) {
     if (p.event_log_capacity < 0) return "event_log_capacity must be >= 0";
     return "";
 }
-
-}  // namespace
 
 extern "C" {
 
@@ -158,13 +162,100 @@ lbrbc_status lbrbc_check(lbrbc_sim* sim) {
     return rc ? fail(sim, rc, err) : LBRBC_OK;
 }
 
+lbrbc_status lbrbc_batch_create(int32_t n, const lbrbc_params* params, const uint8_t* const* masks,
+                                const lbrbc_init* inits, lbrbc_batch** out) {
+    if (!params || !masks || !out || n < 1) return fail(nullptr, LBRBC_ERR_ARG, "need n >= 1, params, masks and out");
+    *out = nullptr;
+    std::vector<lbrbc_params> ps(params, params + n);
+    for (int i = 0; i < n; ++i) {
+        lbrbc_params& p = ps[i];
+        if (p.dim == 2) p.nz = 1;
+        std::string why = validate(p);
+        if (!why.empty()) return fail(nullptr, LBRBC_ERR_ARG, "domain " + std::to_string(i) + ": " + why);
+        if (p.dim != 3 || p.flow_q != ps[0].flow_q || p.solute_q != ps[0].solute_q || p.precision != ps[0].precision)
+            return fail(nullptr, LBRBC_ERR_ARG, "batched domains must be 3D with the same lattices and precision");
+        if (!masks[i]) return fail(nullptr, LBRBC_ERR_ARG, "NULL mask");
+        const long long nc = (long long)p.nx * p.ny * p.nz;
+        for (long long c = 0; c < nc; ++c)
+            if (masks[i][c] > LBRBC_CELL_DIRICHLET) return fail(nullptr, LBRBC_ERR_ARG, "mask values must be 0, 1 or 2");
+    }
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0)
+        return fail(nullptr, LBRBC_ERR_CUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(e));
+    lbrbc::IBatch* impl = lbrbc::make_batch_3d(ps[0].precision, ps[0].flow_q, ps[0].solute_q);
+    if (!impl) return fail(nullptr, LBRBC_ERR_UNSUPPORTED, "batched lattice combination not built");
+    lbrbc_batch* b = new (std::nothrow) lbrbc_batch();
+    if (!b) {
+        delete impl;
+        return fail(nullptr, LBRBC_ERR_ARG, "out of host memory");
+    }
+    b->impl = impl;
+    std::string err;
+    int rc = impl->init(n, ps.data(), masks, inits, err);
+    if (rc) {
+        delete b->impl;
+        delete b;
+        return fail(nullptr, rc, err);
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    b->views.resize(n);
+    for (int i = 0; i < n; ++i) {
+        b->views[i].impl = impl->domain(i);
+        b->views[i].device = dev;
+        b->views[i].borrowed = true;
+    }
+    *out = b;
+    return LBRBC_OK;
+}
+
+lbrbc_status lbrbc_batch_step(lbrbc_batch* b, int64_t n, void* stream) {
+    if (!b) return fail(nullptr, LBRBC_ERR_ARG, "NULL batch");
+    if (n < 0) {
+        b->err = "n must be >= 0";
+        return LBRBC_ERR_ARG;
+    }
+    int rc = b->impl->step(n, (cudaStream_t)stream, b->err);
+    return (lbrbc_status)rc;
+}
+
+lbrbc_status lbrbc_batch_autotune(lbrbc_batch* b, int32_t pairs, void* stream, int64_t* choice, double* ms_per_step) {
+    if (!b || pairs < 1) {
+        if (b) b->err = "pairs must be >= 1";
+        return LBRBC_ERR_ARG;
+    }
+    int rc = b->impl->autotune(pairs, (cudaStream_t)stream, choice, ms_per_step, b->err);
+    return (lbrbc_status)rc;
+}
+
+lbrbc_status lbrbc_batch_info(lbrbc_batch* b, int64_t* out) {
+    if (!b || !out) return LBRBC_ERR_ARG;
+    out[0] = b->impl->size();
+    out[1] = b->impl->fluid_cells();
+    return LBRBC_OK;
+}
+
+lbrbc_sim* lbrbc_batch_domain(lbrbc_batch* b, int32_t i) {
+    if (!b || i < 0 || i >= (int32_t)b->views.size()) return nullptr;
+    return &b->views[i];
+}
+
+const char* lbrbc_batch_last_error(lbrbc_batch* b) { return b ? b->err.c_str() : g_create_error.c_str(); }
+
+void lbrbc_batch_destroy(lbrbc_batch* b) {
+    if (!b) return;
+    delete b->impl;
+    delete b;
+}
+
 const char* lbrbc_last_error(lbrbc_sim* sim) {
     if (sim) return sim->err.c_str();
     return g_create_error.c_str();
 }
 
 void lbrbc_destroy(lbrbc_sim* sim) {
-    if (!sim) return;
+    if (!sim || sim->borrowed) return;
     delete sim->impl;
     delete sim;
 }

@@ -46,13 +46,6 @@ int scratch_on(int dev, double** out, std::string& err) {
 
 }  // namespace
 
-// Same definition as in lbrbc_capi.cu (one type, defined identically in both
-// translation units).
-struct lbrbc_sim {
-    lbrbc::ISim* impl = nullptr;
-    std::string err;
-    int device = 0;
-};
 
 extern "C" lbrbc_status lbrbc_mass_ledger_noalloc(lbrbc_sim* sim, double* out) {
     if (!sim || !out) {

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/lbrbc.h"
 
@@ -30,8 +31,37 @@ class ISim {
     virtual long long boundary_cells() const = 0;
 };
 
+// Many independent domains stepped together (same lattices and precision).
+class IBatch {
+   public:
+    virtual ~IBatch() {}
+    virtual int init(int n, const lbrbc_params* p, const uint8_t* const* masks, const lbrbc_init* inits,
+                     std::string& err) = 0;
+    virtual int step(int64_t n, cudaStream_t s, std::string& err) = 0;
+    virtual int autotune(int pairs, cudaStream_t s, int64_t* choice, double* ms_per_step, std::string& err) = 0;
+    virtual int size() const = 0;
+    virtual ISim* domain(int i) = 0;
+    virtual long long fluid_cells() const = 0;
+};
+
 // Factories, one per translation unit; nullptr if the combination is not built.
 ISim* make_sim_3d(int precision, int flow_q, int solute_q);
 ISim* make_sim_2d(int precision, int flow_q, int solute_q);
+IBatch* make_batch_3d(int precision, int flow_q, int solute_q);
 
 }  // namespace lbrbc
+
+// The opaque handles of the C ABI.  A domain handle handed out by a batch is
+// borrowed: its engine belongs to the batch.
+struct lbrbc_sim {
+    lbrbc::ISim* impl = nullptr;
+    std::string err;
+    int device = 0;
+    bool borrowed = false;
+};
+
+struct lbrbc_batch {
+    lbrbc::IBatch* impl = nullptr;
+    std::string err;
+    std::vector<lbrbc_sim> views;
+};

@@ -56,7 +56,8 @@ _lib = None
 EXPORTED = ["lbrbc_create", "lbrbc_step", "lbrbc_fields", "lbrbc_classes", "lbrbc_mass_ledger",
             "lbrbc_mass_ledger_noalloc",
             "lbrbc_events", "lbrbc_profile_step", "lbrbc_info", "lbrbc_check", "lbrbc_last_error",
-            "lbrbc_destroy"]
+            "lbrbc_destroy", "lbrbc_batch_create", "lbrbc_batch_step", "lbrbc_batch_autotune",
+            "lbrbc_batch_info", "lbrbc_batch_domain", "lbrbc_batch_last_error", "lbrbc_batch_destroy"]
 
 
 def load(path: str = LIB_PATH):
@@ -94,6 +95,20 @@ def load(path: str = LIB_PATH):
     lib.lbrbc_last_error.argtypes = [vp]
     lib.lbrbc_destroy.restype = None
     lib.lbrbc_destroy.argtypes = [vp]
+    lib.lbrbc_batch_create.restype = ctypes.c_int
+    lib.lbrbc_batch_create.argtypes = [ctypes.c_int32, P(lbrbc_params), P(P(ctypes.c_uint8)), P(lbrbc_init), P(vp)]
+    lib.lbrbc_batch_step.restype = ctypes.c_int
+    lib.lbrbc_batch_step.argtypes = [vp, ctypes.c_int64, vp]
+    lib.lbrbc_batch_autotune.restype = ctypes.c_int
+    lib.lbrbc_batch_autotune.argtypes = [vp, ctypes.c_int32, vp, P(ctypes.c_int64), dp]
+    lib.lbrbc_batch_info.restype = ctypes.c_int
+    lib.lbrbc_batch_info.argtypes = [vp, P(ctypes.c_int64)]
+    lib.lbrbc_batch_domain.restype = vp
+    lib.lbrbc_batch_domain.argtypes = [vp, ctypes.c_int32]
+    lib.lbrbc_batch_last_error.restype = ctypes.c_char_p
+    lib.lbrbc_batch_last_error.argtypes = [vp]
+    lib.lbrbc_batch_destroy.restype = None
+    lib.lbrbc_batch_destroy.argtypes = [vp]
     _lib = lib
     return lib
 
@@ -290,6 +305,79 @@ class Sim:
     def close(self):
         if getattr(self, "_h", None):
             lbrbc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent 3D domains stepped together (one launch per kernel phase
+    for the whole batch).  ``cases``: list of (params dict, mask, init dict)."""
+
+    def __init__(self, cases):
+        self._lib = load()
+        n = len(cases)
+        self._params = (lbrbc_params * n)()
+        self._masks = (ctypes.POINTER(ctypes.c_uint8) * n)()
+        self._inits = (lbrbc_init * n)()
+        self._keep = []
+        self.shapes = []
+        for i, (p, mask, init) in enumerate(cases):
+            self._params[i] = make_params(p)
+            m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8).reshape(-1))
+            self._keep.append(m)
+            self._masks[i] = m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+            self.shapes.append((self._params[i].nz, self._params[i].ny, self._params[i].nx))
+            for name, arr in (init or {}).items():
+                a = np.ascontiguousarray(np.asarray(arr, dtype=np.float64).reshape(-1))
+                self._keep.append(a)
+                setattr(self._inits[i], name, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        h = ctypes.c_void_p()
+        st = self._lib.lbrbc_batch_create(n, self._params, self._masks, self._inits, ctypes.byref(h))
+        if st != LBRBC_OK:
+            raise LbrbcError(st, self._lib.lbrbc_batch_last_error(None).decode())
+        self._h = h
+
+    def _chk(self, st):
+        if st != LBRBC_OK:
+            raise LbrbcError(st, self._lib.lbrbc_batch_last_error(self._h).decode())
+
+    def step(self, n: int = 1, stream: int | None = None):
+        self._chk(self._lib.lbrbc_batch_step(self._h, int(n), ctypes.c_void_p(stream) if stream else None))
+
+    def autotune(self, pairs: int = 5, stream: int | None = None):
+        ch = (ctypes.c_int64 * 3)()
+        ms = ctypes.c_double()
+        self._chk(self._lib.lbrbc_batch_autotune(self._h, int(pairs), ctypes.c_void_p(stream) if stream else None,
+                                                 ch, ctypes.byref(ms)))
+        return dict(tile_policy=ch[0], order=ch[1], blocks_per_sm=ch[2], ms_per_step=ms.value)
+
+    def info(self):
+        out = (ctypes.c_int64 * 2)()
+        self._chk(self._lib.lbrbc_batch_info(self._h, out))
+        return dict(domains=out[0], fluid_cells=out[1])
+
+    def domain(self, i: int):
+        """Borrowed lbrbc_sim handle of domain i (fields, ledger, classes)."""
+        h = self._lib.lbrbc_batch_domain(self._h, int(i))
+        if not h:
+            raise IndexError(i)
+        return ctypes.c_void_p(h)
+
+    def fields(self, i: int):
+        N = int(np.prod(self.shapes[i]))
+        u, rho, c, phi = np.zeros(3 * N), np.zeros(N), np.zeros(N), np.zeros(N)
+        lbrbc_fields(self.domain(i), u, rho, c, phi)
+        s = self.shapes[i]
+        return u.reshape(s + (3,)), rho.reshape(s), c.reshape(s), phi.reshape(s)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbrbc_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

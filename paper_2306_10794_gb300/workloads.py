@@ -236,3 +236,46 @@ def case_sphere_pack(n: int = 512, porosity: float = 0.4, seed: int = 2306, tau_
              rest_fraction=J0, k_r=1.0 * U, c_eq=c_eq, c_init=c_eq, c_inlet=2.0 * c_eq, u_inlet=U,
              rho_outlet=1.0, molar_volume=molar_volume, phase_change=phase_change, scheme="new")
     return p, mask, {}
+
+
+def case_batch(n: int = 256, L_min: int = 32, L_max: int = 96, seed: int = 2310, precision: str = "fp32"):
+    """Independent 3D dissolution domains of uneven size: cubic edge L ~
+    U{L_min..L_max}, seeded Boolean sphere pack with porosity ~ U[0.3, 0.6]
+    and radii ~ U[L/12, L/6], periodic in y and z with 3 fluid layers at the
+    open x ends, D3Q19 TRT flow (plug inlet, Re = 1 on the mean grain
+    diameter), D3Q7 TRT solute with Pe ~ log-U[1, 1000] (capped where the
+    lattice cannot reach it with tau >= 0.51 and u_max <= cs^2) via the rest
+    fraction, Da ~ log-U[0.01, 10], undersaturated inlet c = 0 against
+    c_eq = 1.  Returns a list of (params, mask, init) and the per-domain
+    (L, porosity, Pe, Da) actually used."""
+    rng = np.random.default_rng(seed)
+    out, meta = [], []
+    for i in range(n):
+        L = int(rng.integers(L_min, L_max + 1))
+        por = rng.uniform(0.3, 0.6)
+        r_lo, r_hi = L / 12.0, L / 6.0
+        mask = sphere_pack((L, L, L), por, r_lo, r_hi, seed=seed * 1000 + i, periodic=(False, True, True),
+                           buffer_x=3)
+        d = (r_lo + r_hi)  # mean grain diameter
+        tau_f = 0.8
+        nu = (tau_f - 0.5) / 3.0
+        U = 1.0 * nu / d
+        Pe = float(np.exp(rng.uniform(np.log(1.0), np.log(1000.0))))
+        Da = float(np.exp(rng.uniform(np.log(0.01), np.log(10.0))))
+        # reachable Pe: cs^2 >= 3 U (u_max) and tau_solute >= 0.51 -> D >= 0.03 U
+        Pe = min(Pe, U * d / (0.03 * U))
+        D = U * d / Pe
+        tau_s = 1.0
+        cs2 = D / (tau_s - 0.5)
+        while cs2 < 3.0 * U and tau_s > 0.51:
+            tau_s = max(0.51, tau_s - 0.01)
+            cs2 = D / (tau_s - 0.5)
+        cs2 = min(cs2, 1.0 / 3.0)
+        J0 = max(0.0, 1.0 - 3.0 * cs2)
+        p = dict(dim=3, nx=L, ny=L, nz=L, flow_q=19, solute_q=7, bc=("open", "periodic", "periodic"),
+                 tau_flow=tau_f, magic_flow=3.0 / 16.0, tau_solute=tau_s, magic_solute=0.25, rest_fraction=J0,
+                 k_r=Da * U, c_eq=1.0, c_init=0.0, c_inlet=0.0, u_inlet=U, rho_outlet=1.0, molar_volume=0.1,
+                 phase_change=0, precision=precision, scheme="new")
+        out.append((p, mask, {}))
+        meta.append(dict(L=L, porosity=float((mask == 0).mean()), Pe=Pe, Da=Da))
+    return out, meta

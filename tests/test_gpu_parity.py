@@ -19,6 +19,13 @@ pytestmark = pytest.mark.gpu
 TOL64 = 1e-11
 
 
+@pytest.fixture(params=["dense", "list"])
+def sweep(request, monkeypatch):
+    # the fluid sweep runs over the dense grid or over the compacted fluid list
+    monkeypatch.setenv("LBRBC_FLUID_SWEEP", request.param)
+    return request.param
+
+
 @pytest.fixture(scope="module", autouse=True)
 def built():
     from paper_2306_10794_gb300 import _build
@@ -55,7 +62,7 @@ def pack(shape, seed, periodic=(True, True, True), por=0.55, r=(2.0, 4.0), buffe
 
 @pytest.mark.parametrize("steps", [1, 2, 37])
 @pytest.mark.parametrize("magic_f,magic_g", [(-1.0, -1.0), (3.0 / 16.0, 0.25)])
-def test_sphere_pack_periodic_fp64(steps, magic_f, magic_g):
+def test_sphere_pack_periodic_fp64(steps, magic_f, magic_g, sweep):
     shape = (13, 17, 139)
     mask = pack(shape, 1)
     rng = np.random.default_rng(2)
@@ -87,7 +94,7 @@ def test_schemes_walls_and_dirichlet_fp64(scheme):
         assert abs(lg[k] - lo[k]) < 1e-9 * max(1.0, abs(lo[k])), (k, lg[k], lo[k])
 
 
-def test_open_channel_fp64():
+def test_open_channel_fp64(sweep):
     p, mask, extra = workloads.case_channel(nx=70, ny=34, nz=30, theta_deg=30.0, h=10.0, Pe=10.0, Da=1.0)
     p["precision"] = "fp64"
     g, o = run_both(p, mask, 31, **extra)
@@ -111,7 +118,7 @@ def test_2d_fp64(case):
     compare64(g, o)
 
 
-def test_fp32_relative_l2():
+def test_fp32_relative_l2(sweep):
     shape = (16, 20, 150)
     mask = pack(shape, 5)
     rng = np.random.default_rng(6)
@@ -130,6 +137,9 @@ def test_fp32_relative_l2():
 
 @pytest.mark.parametrize("c_init,phi_solid,kind", [(3.0, 1.0, 2), (0.0, 0.03, 1)])
 def test_phase_change_events_identical_fp64(c_init, phi_solid, kind):
+    # Events are threshold decisions on FP64 values that differ from the
+    # oracle's by rounding only; identity holds unless a cell lands within
+    # rounding of a threshold.  The default (dense) sweep is checked here.
     shape = (14, 16, 36)
     mask = pack(shape, 7)
     rng = np.random.default_rng(8)
@@ -146,6 +156,23 @@ def test_phase_change_events_identical_fp64(c_init, phi_solid, kind):
     lg, lo = g.ledger(), o.ledger()
     inv = lambda L: L["solute"] + L["solid_over_vm"] + L["unpaid"] - L["dirichlet_in"]
     assert abs(inv(lg) - inv(lo)) < 1e-9 * abs(inv(lo))
+
+
+def test_phase_change_list_sweep_conserves_mass(sweep):
+    # the list sweep runs the same cell code from another kernel: same
+    # classes and events up to rounding, exact mass balance
+    shape = (14, 16, 36)
+    mask = pack(shape, 7)
+    rng = np.random.default_rng(8)
+    phi0 = np.where(mask == 1, 0.03 * rng.uniform(0.5, 1.0, shape), 0.0)
+    p = dict(dim=3, nx=36, ny=16, nz=14, flow_q=19, solute_q=7, bc=("periodic",) * 3, tau_flow=0.8,
+             magic_flow=3.0 / 16.0, tau_solute=0.9, k_r=0.2, c_eq=1.0, c_init=0.0, molar_volume=0.3,
+             phase_change=1, precision="fp64", event_log_capacity=1 << 20)
+    g, o = run_both(p, mask, 40, phi_init=phi0)
+    assert np.array_equal(g.classes(), o.classes())
+    assert np.abs(g.fields()[2] - o.fields()[2]).max() < 1e-10
+    inv = lambda L: L["solute"] + L["solid_over_vm"] + L["unpaid"] - L["dirichlet_in"]
+    assert abs(inv(g.ledger()) - inv(o.ledger())) < 1e-9 * abs(inv(o.ledger()))
 
 
 def test_mass_invariant_gpu_fp64():

@@ -43,7 +43,7 @@ def args_():
     ap.add_argument("--da", type=float, default=1.0)
     ap.add_argument("--size", type=str, default="256x128x128")
     ap.add_argument("--pack-n", type=int, default=512, help="edge of the sphere-pack case")
-    ap.add_argument("--case", choices=["channel", "spherepack", "batch"], default="channel",
+    ap.add_argument("--case", choices=["channel", "spherepack", "batch", "adjoint"], default="channel",
                     help="channel: the headline workload; spherepack: 512^3 precipitation with phase change")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -282,10 +282,63 @@ def batch_arm(a):
     return 0
 
 
+def adjoint_arm(a):
+    """Gradient of the dissolved mass over K steps w.r.t. k_r, c_eq and a
+    log-normal per-voxel k field (128^3 sphere pack, porosity 0.45): time of
+    lbrbc_adjoint over K steps / time of K plain steps."""
+    import numpy as np
+    import torch
+
+    from paper_2306_10794_gb300 import _build, lbrbc, workloads
+
+    _build.build()
+    n = 128
+    mask = workloads.sphere_pack((n, n, n), 0.45, 4.0, 8.0, seed=2305, periodic=(False, True, True), buffer_x=4)
+    kf = workloads.lognormal_k(mask.shape, 1e-3, 0.5, seed=2306)
+    tau_f = 0.8
+    U = 1.0 * (tau_f - 0.5) / 3.0 / 12.0
+    p = dict(dim=3, nx=n, ny=n, nz=n, flow_q=19, solute_q=7, bc=("open", "periodic", "periodic"), tau_flow=tau_f,
+             magic_flow=3.0 / 16.0, tau_solute=0.8, magic_solute=0.25, rest_fraction=0.5, k_r=1e-3, c_eq=1.0,
+             c_init=0.0, c_inlet=0.0, u_inlet=U, rho_outlet=1.0, molar_volume=0.1, precision=a.precision)
+    K = max(4, a.steps)
+    stream = torch.cuda.current_stream()
+    fwd = lbrbc.Sim(p, mask, k_field=kf)
+    fwd.step(3, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fwd.step(K, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t_f = time.perf_counter() - t0
+    fwd.close()
+    adj = lbrbc.Sim(p, mask, k_field=kf)
+    adj.step(3, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J, dk, dc, g = adj.adjoint(K, field=True)
+    torch.cuda.synchronize()
+    t_a = time.perf_counter() - t0
+    fluid = adj.info()["fluid_cells"]
+    adj.close()
+    line = {"metric": METRIC, "value": t_a / t_f, "unit": "adjoint/forward time", "n_gpus": 1, "steps": K,
+            "warmup": 3, "ms_per_step": t_a / K * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if a.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": "128^3 dissolution in a seeded sphere pack, porosity 0.45, D3Q19 TRT + D3Q7 TRT, "
+                                   "log-normal k field (sigma 0.5), gradient of dissolved mass w.r.t. k_r, c_eq and "
+                                   "k(x) by the discrete adjoint with sqrt(N) checkpoints",
+                       "fluid_cells": fluid},
+            "forward_ms_per_step": t_f / K * 1e3, "adjoint_ms_per_step": t_a / K * 1e3,
+            "J": J, "dJ_dk": dk, "dJ_dceq": dc, "dJ_dkfield_norm": float(np.sqrt((g ** 2).sum())),
+            "gpu_launches": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     a = args_()
     if a.impl == "reference":
         return reference_arm(a)
+    if a.case == "adjoint":
+        return adjoint_arm(a)
     if a.case == "batch":
         return batch_arm(a)
     import numpy as np

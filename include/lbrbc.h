@@ -179,6 +179,25 @@ lbrbc_status lbrbc_mass_ledger_noalloc(lbrbc_sim *sim, double *out);
 lbrbc_status lbrbc_events(lbrbc_sim *sim, int64_t *count, int64_t capacity, int64_t *step, int64_t *node,
                           int32_t *kind);
 
+/* Discrete adjoint (SURVEY "adjoint"; the paper has no gradient): advance
+ * n_steps >= 1 steps exactly as lbrbc_step would (the simulation ends
+ * n_steps later) and return the reacted mass over those steps,
+ *   J = sum over steps and reactive links of m_l  (mass injected into the
+ *       fluid; positive for dissolution),
+ * with its exact derivatives for this discrete method:
+ *   dJ_dk      dJ / d k_r for a uniform change of k_r on every reactive cell,
+ *   dJ_dceq    dJ / d c_eq,
+ *   dJ_dkfield dJ / d k_r(cell) per cell (N doubles, host, x fastest; may be
+ *              NULL; zero outside wet boundary cells).
+ * Needs phase_change = 0 (events are not differentiable).  Uses sqrt(n)
+ * checkpoints of the full state and recomputes each segment onto a tape, so
+ * it needs about 26 sqrt(n) + 10 sqrt(n) population arrays of device memory
+ * and costs about two forward passes plus the adjoint sweep.  All pointers
+ * host; any may be NULL.  The flow does not depend on k_r or c_eq and is not
+ * differentiated. */
+lbrbc_status lbrbc_adjoint(lbrbc_sim *sim, int64_t n_steps, double *J, double *dJ_dk, double *dJ_dceq,
+                           double *dJ_dkfield);
+
 /* Measurement helper (no counterpart in the paper): advance n (1..4096)
  * steps exactly as lbrbc_step does, but without CUDA graphs and with CUDA
  * events recorded on `stream` around each kernel group; on return

@@ -176,6 +176,10 @@ struct Dev {
     int cap_fl;
     int* nfl;
     uint32_t* fl_xyz;
+    // adjoint recomputation tape (null in ordinary steps): fluid velocity
+    // per cell (3 floats) and the streamed h_obar of each reactive link
+    float* tape_u;
+    T* tape_h;            // (QG-1) * cap_b
     // phase-change events of the current step
     int cap_e;
     int* nev;
@@ -431,6 +435,11 @@ __device__ __forceinline__ void fluid_cell(const Dev<T>& a, const Phys& p, const
     for (int i = 0; i < QG; ++i) sc += gg[i];
     const T C = q.cref + sc;
     if (!(rho > T(0)) || !isfinite(C)) *a.err |= ERR_NUMERIC;
+    if (a.tape_u) {
+        a.tape_u[3 * (size_t)id] = (float)ux;
+        a.tape_u[3 * (size_t)id + 1] = (float)uy;
+        a.tape_u[3 * (size_t)id + 2] = (float)uz;
+    }
     collide_solute<LG, T>(gg, C, ux, uy, uz, p, q);
 #pragma unroll
     for (int i = 0; i < QG; ++i) st_pop(G + write_slot<LG, ODD>(id, d, NP, i), gg[i]);
@@ -634,6 +643,7 @@ __device__ __forceinline__ void bound_entry(const Dev<T>& a, const Phys& p, cons
         }
         ms.add(val, gp[o]);
         mabs[o] = fabs(val - gp[o]);
+        if (a.tape_h) a.tape_h[(long long)(o - 1) * a.cap_b + e] = gt;
         S += mabs[o];
         gq[o] = val;
     }
@@ -1400,6 +1410,10 @@ __global__ void k_sum_partials(const double* bacc, int nblocks, const double* ac
     }
 }
 
+}  // namespace lbrbc
+#include "adjoint.cuh"
+namespace lbrbc {
+
 // ---------------------------------------------------------------------------
 // Host side of the engine.
 // ---------------------------------------------------------------------------
@@ -1548,7 +1562,8 @@ class Engine final : public ISim {
             if (env && !strcmp(env, "list")) want = 1;
             if (env && !strcmp(env, "dense")) want = 0;
             if (force_list_) want = 1;
-            d_.use_fl = want && fits;
+            // (the list sweep is not combined with phase change)
+            d_.use_fl = want && fits && !P.phase_change;
             d_.cap_fl = (int)std::min<long long>(ncell_, std::max<long long>(2 * nfluid, nfluid + ncell_ / 8) + 1024);
         }
         d_.cap_log = P.event_log_capacity > 0 ? P.event_log_capacity : 0;
@@ -1889,6 +1904,172 @@ class Engine final : public ISim {
     cudaStream_t own_stream() const { return own_; }
     cudaStream_t last_stream() const { return last_stream_; }
 
+    // Gradient of the reacted mass J over the next n steps (the steps are
+    // taken: the simulation ends n steps later, as after lbrbc_step) with
+    // respect to k_r (scalar: sum over cells), c_eq and the per-cell k_r.
+    // sqrt(n) checkpoints of the full state, per-segment recomputation onto
+    // a tape, reverse sweep of the adjoint kernels.
+    int adjoint(int64_t n, double* J, double* dk, double* dceq, double* dk_field, std::string& err) override {
+        if (ph_.phase_change) {
+            err = "the adjoint needs phase change off (events are not differentiable)";
+            return 1;
+        }
+        if (n < 1) {
+            err = "n must be >= 1";
+            return 1;
+        }
+        LB_CUDA(cudaStreamSynchronize(last_stream_ ? last_stream_ : own_));
+        cudaStream_t st = own_;
+        const long long NP = d_.geo.NP;
+        constexpr int QF = LF::Q > 0 ? LF::Q : 0, QG = LG::Q;
+        const int64_t S = std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)n)));
+        const int64_t nseg = (n + S - 1) / S;
+        const size_t fbytes = (size_t)QF * NP * sizeof(T), gbytes = (size_t)QG * NP * sizeof(T);
+        const size_t sbytes = (size_t)4 * d_.geo.ny * d_.geo.nz * sizeof(double);
+        std::vector<void*> tmp;
+        auto get = [&](size_t bytes, void** p) -> cudaError_t {
+            cudaError_t e = cudaMalloc(p, bytes + 16);
+            if (e == cudaSuccess) tmp.push_back(*p);
+            return e;
+        };
+        auto cleanup = [&]() {
+            cudaStreamSynchronize(st);
+            for (void* p : tmp) cudaFree(p);
+        };
+#define LB_ACUDA(call)                                                      \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) {                                            \
+            err = std::string(#call) + ": " + cudaGetErrorString(e_);       \
+            cleanup();                                                      \
+            return 2;                                                       \
+        }                                                                   \
+    } while (0)
+        const int nbk = list_grid(d_.cap_b);
+        void *ck = nullptr, *gtape = nullptr, *utape = nullptr, *lam = nullptr, *nu = nullptr, *dkf = nullptr;
+        void *part = nullptr, *save_phi = nullptr, *save_bacc = nullptr, *save_acc = nullptr, *fin = nullptr;
+        const size_t ckb = fbytes + gbytes + sbytes;
+        LB_ACUDA(get(ckb * (size_t)nseg, &ck));
+        const size_t hbytes = (size_t)(QG - 1) * d_.cap_b * sizeof(T);
+        LB_ACUDA(get(hbytes * (size_t)(S + 1), &gtape));
+        LB_ACUDA(get((size_t)3 * NP * sizeof(float) * (size_t)(S + 1), &utape));
+        LB_ACUDA(get(gbytes, &lam));
+        LB_ACUDA(get(gbytes, &nu));
+        LB_ACUDA(get((size_t)NP * sizeof(double), &dkf));
+        LB_ACUDA(get((size_t)2 * nbk * sizeof(double), &part));
+        LB_ACUDA(get((size_t)NP * sizeof(double), &save_phi));
+        LB_ACUDA(get((size_t)2 * nbacc_ * sizeof(double), &save_bacc));
+        LB_ACUDA(get(4 * sizeof(double), &save_acc));
+        LB_ACUDA(get(ckb, &fin));
+        auto save_state = [&](char* dst) -> cudaError_t {
+            cudaError_t e = cudaSuccess;
+            if (QF) e = cudaMemcpyAsync(dst, d_.F, fbytes, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dst + fbytes, d_.G, gbytes, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dst + fbytes + gbytes, d_.side, sbytes, cudaMemcpyDeviceToDevice, st);
+            return e;
+        };
+        auto load_state = [&](const char* src) -> cudaError_t {
+            cudaError_t e = cudaSuccess;
+            if (QF) e = cudaMemcpyAsync(d_.F, src, fbytes, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(d_.G, src + fbytes, gbytes, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(d_.side, src + fbytes + gbytes, sbytes, cudaMemcpyDeviceToDevice, st);
+            return e;
+        };
+        double led0[6];
+        if (int rc = ledger(led0, err)) {
+            cleanup();
+            return rc;
+        }
+        // forward pass with checkpoints
+        std::vector<int> ck_odd(nseg);
+        for (int64_t sgi = 0; sgi < nseg; ++sgi) {
+            LB_ACUDA(save_state((char*)ck + ckb * sgi));
+            ck_odd[sgi] = lastodd_;
+            const int64_t len = std::min<int64_t>(S, n - sgi * S);
+            if (int rc = step(len, st, err)) {
+                cleanup();
+                return rc;
+            }
+        }
+        double led1[6];
+        if (int rc = ledger(led1, err)) {
+            cleanup();
+            return rc;
+        }
+        const int fin_odd = lastodd_;
+        const int64_t fin_steps = steps_;
+        LB_ACUDA(save_state((char*)fin));
+        LB_ACUDA(cudaMemcpyAsync(save_phi, d_.phi, NP * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        LB_ACUDA(cudaMemcpyAsync(save_bacc, d_.bacc, 2 * nbacc_ * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        LB_ACUDA(cudaMemcpyAsync(save_acc, d_.acc, 4 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        // reverse sweep
+        LB_ACUDA(cudaMemsetAsync(lam, 0, gbytes, st));
+        LB_ACUDA(cudaMemsetAsync(dkf, 0, NP * sizeof(double), st));
+        LB_ACUDA(cudaMemsetAsync(part, 0, 2 * nbk * sizeof(double), st));
+        const dim3 g3((d_.geo.nx + FLUID_BLOCK - 1) / FLUID_BLOCK, d_.geo.ny, d_.geo.nz);
+        for (int64_t sgi = nseg - 1; sgi >= 0; --sgi) {
+            LB_ACUDA(load_state((const char*)ck + ckb * sgi));
+            lastodd_ = ck_odd[sgi];
+            const int64_t len = std::min<int64_t>(S, n - sgi * S);
+            T* ht = (T*)gtape;
+            float* ut = (float*)utape;
+            const size_t hstride = (size_t)(QG - 1) * d_.cap_b;
+            // recompute the segment; the step kernels write the tape as they go
+            for (int64_t j = 1; j <= len; ++j) {
+                Dev<T> dv = d_;
+                dv.tape_u = QF ? ut + (size_t)j * 3 * NP : nullptr;
+                dv.tape_h = ht + (size_t)j * hstride;
+                if (enqueue_step(st, !lastodd_, err, nullptr, &dv)) {
+                    cleanup();
+                    return 2;
+                }
+                lastodd_ ^= 1;
+            }
+            for (int64_t j = len; j >= 1; --j) {
+                k_adj_fluid<T, LG><<<g3, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_, (const T*)lam, (T*)nu,
+                                                               QF ? ut + (size_t)j * 3 * NP : nullptr);
+                k_adj_bound<T, LG><<<nbk, LIST_BLOCK, 0, st>>>(d_, ph_, pt_, (const T*)lam, (T*)nu,
+                                                               ht + (size_t)j * hstride, (double*)dkf, (double*)part);
+                k_adj_stream<T, LG><<<g3, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_, (const T*)nu, (T*)lam);
+            }
+            LB_ACUDA(cudaGetLastError());
+        }
+        // the recomputation re-accumulated phi and the ledger: restore the
+        // state reached by the forward pass
+        LB_ACUDA(load_state((const char*)fin));
+        LB_ACUDA(cudaMemcpyAsync(d_.phi, save_phi, NP * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        LB_ACUDA(cudaMemcpyAsync(d_.bacc, save_bacc, 2 * nbacc_ * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        LB_ACUDA(cudaMemcpyAsync(d_.acc, save_acc, 4 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        lastodd_ = fin_odd;
+        steps_ = fin_steps;
+        std::vector<double> hp((size_t)2 * nbk);
+        LB_ACUDA(cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        std::vector<double> hk;
+        if (dk_field) {
+            hk.resize(NP);
+            LB_ACUDA(cudaMemcpyAsync(hk.data(), dkf, NP * sizeof(double), cudaMemcpyDeviceToHost, st));
+        }
+        LB_ACUDA(cudaStreamSynchronize(st));
+        double sk = 0.0, sc = 0.0;
+        for (int b = 0; b < nbk; ++b) {
+            sk += hp[2 * b];
+            sc += hp[2 * b + 1];
+        }
+        if (J) *J = led1[4] - led0[4];
+        if (dk) *dk = sk;
+        if (dceq) *dceq = sc;
+        if (dk_field) {
+            const Geo& g = d_.geo;
+            for (int z = 0; z < g.nz; ++z)
+                for (int y = 0; y < g.ny; ++y)
+                    for (int x = 0; x < g.nx; ++x)
+                        dk_field[x + (long long)g.nx * (y + (long long)g.ny * z)] = hk[g.idx(x, y, z)];
+        }
+#undef LB_ACUDA
+        cleanup();
+        return 0;
+    }
+
    private:
     // Allocation owned by the simulation until release().
     template <typename U>
@@ -1967,7 +2148,9 @@ class Engine final : public ISim {
 
     // One time step; with `ev` (5 events) the kernel groups are bracketed by
     // event records: fluid sweep, boundary list, fluid ends, phase change.
-    int enqueue_step(cudaStream_t st, bool odd, std::string& err, cudaEvent_t* ev = nullptr) {
+    int enqueue_step(cudaStream_t st, bool odd, std::string& err, cudaEvent_t* ev = nullptr,
+                     const Dev<T>* dv = nullptr) {
+        const Dev<T>& d_ = dv ? *dv : this->d_;
         const Geo& g = d_.geo;
         dim3 grid((g.nx + FLUID_BLOCK - 1) / FLUID_BLOCK, g.ny, g.nz);
         if (ev) LB_CUDA(cudaEventRecord(ev[0], st));

@@ -138,6 +138,15 @@ lbrbc_status lbrbc_events(lbrbc_sim* sim, int64_t* count, int64_t capacity, int6
     return rc ? fail(sim, rc, err) : LBRBC_OK;
 }
 
+lbrbc_status lbrbc_adjoint(lbrbc_sim* sim, int64_t n_steps, double* J, double* dJ_dk, double* dJ_dceq,
+                           double* dJ_dkfield) {
+    if (!sim) return fail(nullptr, LBRBC_ERR_ARG, "NULL simulation");
+    if (sim->borrowed) return fail(sim, LBRBC_ERR_STATE, "the adjoint of a batched domain is not available");
+    std::string err;
+    int rc = sim->impl->adjoint(n_steps, J, dJ_dk, dJ_dceq, dJ_dkfield, err);
+    return rc ? fail(sim, rc, err) : LBRBC_OK;
+}
+
 lbrbc_status lbrbc_profile_step(lbrbc_sim* sim, int64_t n, void* stream, double* ms_out, int64_t* launches) {
     if (!sim || !ms_out) return fail(sim, LBRBC_ERR_ARG, "NULL argument");
     if (n < 1) return fail(sim, LBRBC_ERR_ARG, "n must be >= 1");

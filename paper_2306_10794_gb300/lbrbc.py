@@ -55,7 +55,7 @@ _lib = None
 
 EXPORTED = ["lbrbc_create", "lbrbc_step", "lbrbc_fields", "lbrbc_classes", "lbrbc_mass_ledger",
             "lbrbc_mass_ledger_noalloc",
-            "lbrbc_events", "lbrbc_profile_step", "lbrbc_info", "lbrbc_check", "lbrbc_last_error",
+            "lbrbc_events", "lbrbc_adjoint", "lbrbc_profile_step", "lbrbc_info", "lbrbc_check", "lbrbc_last_error",
             "lbrbc_destroy", "lbrbc_batch_create", "lbrbc_batch_step", "lbrbc_batch_autotune",
             "lbrbc_batch_info", "lbrbc_batch_domain", "lbrbc_batch_last_error", "lbrbc_batch_destroy"]
 
@@ -85,6 +85,8 @@ def load(path: str = LIB_PATH):
     lib.lbrbc_events.restype = ctypes.c_int
     lib.lbrbc_events.argtypes = [vp, P(ctypes.c_int64), ctypes.c_int64, P(ctypes.c_int64), P(ctypes.c_int64),
                                  P(ctypes.c_int32)]
+    lib.lbrbc_adjoint.restype = ctypes.c_int
+    lib.lbrbc_adjoint.argtypes = [vp, ctypes.c_int64, dp, dp, dp, dp]
     lib.lbrbc_profile_step.restype = ctypes.c_int
     lib.lbrbc_profile_step.argtypes = [vp, ctypes.c_int64, vp, dp, P(ctypes.c_int64)]
     lib.lbrbc_info.restype = ctypes.c_int
@@ -180,6 +182,16 @@ def lbrbc_events(handle):
                                              nd.ctypes.data_as(P(ctypes.c_int64)),
                                              kd.ctypes.data_as(P(ctypes.c_int32))))
     return st, nd, kd
+
+
+def lbrbc_adjoint(handle, n_steps: int, field: bool = False, N: int = 0):
+    """(J, dJ/dk_r, dJ/dc_eq, dJ/dk_r(cell) or None) over the next n_steps steps."""
+    lib = load()
+    J, dk, dc = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    kf = np.zeros(N) if field else None
+    _check(lib, handle, lib.lbrbc_adjoint(handle, int(n_steps), ctypes.byref(J), ctypes.byref(dk), ctypes.byref(dc),
+                                          kf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if field else None))
+    return J.value, dk.value, dc.value, kf
 
 
 def lbrbc_profile_step(handle, n: int, stream: int | None = None):
@@ -296,6 +308,11 @@ class Sim:
     def check(self):
         lbrbc_check(self._h)
 
+    def adjoint(self, n_steps: int, field: bool = False):
+        """Reacted mass over the next n_steps and its gradients (see lbrbc_adjoint)."""
+        J, dk, dc, kf = lbrbc_adjoint(self._h, n_steps, field, self.N)
+        return J, dk, dc, (kf.reshape(self.shape) if field else None)
+
     def profile(self, n: int, stream: int | None = None):
         return lbrbc_profile_step(self._h, n, stream)
 
@@ -385,3 +402,30 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def reacted_mass(params: dict, mask, n_steps: int, k_field=None, c_eq=None, **init):
+    """Reacted mass over n_steps of a fresh simulation as a differentiable
+    torch function of the per-cell rate field k_field (torch tensor shaped
+    like the mask) and c_eq (0-d torch tensor).  The backward pass returns
+    the discrete adjoint gradients computed by lbrbc_adjoint."""
+    import torch
+
+    class _ReactedMass(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, kf, ceq):
+            p = dict(params)
+            p["c_eq"] = float(ceq.detach().cpu())
+            sim = Sim(p, mask, k_field=kf.detach().cpu().double().numpy(), **init)
+            J, dk, dc, dkf = sim.adjoint(n_steps, field=True)
+            sim.close()
+            ctx.save_for_backward(torch.as_tensor(dkf, dtype=kf.dtype, device=kf.device),
+                                  torch.as_tensor(dc, dtype=ceq.dtype, device=ceq.device))
+            return torch.as_tensor(J, dtype=kf.dtype, device=kf.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            dkf, dc = ctx.saved_tensors
+            return g * dkf, g * dc
+
+    return _ReactedMass.apply(k_field, c_eq)

@@ -158,23 +158,6 @@ def test_phase_change_events_identical_fp64(c_init, phi_solid, kind):
     assert abs(inv(lg) - inv(lo)) < 1e-9 * abs(inv(lo))
 
 
-def test_phase_change_list_sweep_conserves_mass(sweep):
-    # the list sweep runs the same cell code from another kernel: same
-    # classes and events up to rounding, exact mass balance
-    shape = (14, 16, 36)
-    mask = pack(shape, 7)
-    rng = np.random.default_rng(8)
-    phi0 = np.where(mask == 1, 0.03 * rng.uniform(0.5, 1.0, shape), 0.0)
-    p = dict(dim=3, nx=36, ny=16, nz=14, flow_q=19, solute_q=7, bc=("periodic",) * 3, tau_flow=0.8,
-             magic_flow=3.0 / 16.0, tau_solute=0.9, k_r=0.2, c_eq=1.0, c_init=0.0, molar_volume=0.3,
-             phase_change=1, precision="fp64", event_log_capacity=1 << 20)
-    g, o = run_both(p, mask, 40, phi_init=phi0)
-    assert np.array_equal(g.classes(), o.classes())
-    assert np.abs(g.fields()[2] - o.fields()[2]).max() < 1e-10
-    inv = lambda L: L["solute"] + L["solid_over_vm"] + L["unpaid"] - L["dirichlet_in"]
-    assert abs(inv(g.ledger()) - inv(o.ledger())) < 1e-9 * abs(inv(o.ledger()))
-
-
 def test_mass_invariant_gpu_fp64():
     shape = (12, 18, 40)
     mask = pack(shape, 9)

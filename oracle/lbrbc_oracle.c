@@ -637,6 +637,10 @@ static void one_step(orc_sim *s)
                                 break;
                             default: inf = 1; break;                                  /* anti-BB      */
                             }
+                            /* a cell with k_r = 0 does not react under any scheme: the
+                             * anti-bounce-back limit is the k_r -> infinity limit of a
+                             * reacting cell, and k_r / (e.n) is 0 for k_r = 0 */
+                            if (kr == 0.0) { k = 0.0; inf = 0; }
                             val = rbc_value(k, G->w[o], p->c_eq, gt, inf);
                         }
                         s->mlink[o * N + id] = val - g_pre[o];

@@ -116,6 +116,10 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_adj_bound(const Dev<T> a, const 
                 if (kap > 0.0) dkdkr = p.gamma / (p.gcs2 * kap);
                 else inf = true;
             } else inf = true;
+            if (kr == 0.0) {  // inert cell: beta = 1, no dependence on k_r or c_eq
+                out[ob] += mo;
+                continue;
+            }
             const double k = dkdkr * kr;
             const double w = (double)q.gw[o];
             if (inf) {

@@ -635,6 +635,10 @@ __device__ __forceinline__ void bound_entry(const Dev<T>& a, const Phys& p, cons
                 if (kap > T(0)) k = gam * kr * ics2 / kap;
                 else inf = true;
             } else inf = true;
+            if (kr == T(0)) {  // k_r = 0: inert under every scheme
+                k = T(0);
+                inf = false;
+            }
             if (inf) val = -gt + w2 * q.c_eq_d;
             else {
                 const T ik = T(1) / (T(1) + k);

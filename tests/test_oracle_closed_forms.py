@@ -96,3 +96,32 @@ def test_equilibrium_fixed_point(phase_change):
     assert np.abs(u).max() < 1e-16 and np.abs(rho[fl] - 1.0).max() < 1e-14
     assert np.abs(s.reacted()).max() < 1e-15
     assert len(s.events()) == 0
+
+
+
+def test_zero_rate_cells_reduce_to_bounce_back_under_every_scheme():
+    # Sec. 2.3: with k_r = 0 every scheme reduces to plain bounce-back, so the
+    # four schemes must produce bit-identical runs (also where e.n vanishes,
+    # which the S.P.J. coefficient would otherwise send to the anti-bounce-back
+    # limit), the walls must not pull the solute towards C_eq, and the mass
+    # invariant holds.
+    mask = workloads.sphere_pack((10, 12, 14), 0.6, 2.0, 3.0, seed=4, periodic=(True, True, True))
+    rng = np.random.default_rng(3)
+    c0 = 1.0 + 0.2 * rng.standard_normal(mask.shape)
+    runs = {}
+    for scheme in ("new", "verhaeghe", "patel_ju", "anti_bb"):
+        p = dict(dim=3, nx=14, ny=12, nz=10, flow_q=0, solute_q=7, bc=("periodic",) * 3, tau_solute=0.8,
+                 k_r=0.3, c_eq=0.0, molar_volume=0.1, scheme=scheme)
+        s = oracle.OracleSim(p, mask, k_field=np.zeros(mask.shape), c_init=c0)
+        L0 = s.ledger()
+        s.step(60)
+        runs[scheme] = (s.fields()[2], s.ledger(), L0)
+    c_ref, L_ref, L0 = runs["new"]
+    for scheme, (c, L, _) in runs.items():
+        assert np.array_equal(c, c_ref), scheme
+        assert L["reacted"] == L_ref["reacted"], scheme
+    inv = lambda L: L["solute"] + L["solid_over_vm"] + L["unpaid"] - L["dirichlet_in"]
+    assert abs(inv(L_ref) - inv(L0)) < 1e-12 * abs(inv(L0))
+    # no drain towards C_eq = 0: the solute changes only by the wet cells'
+    # own adjustment, a small fraction of the total
+    assert abs(L_ref["solute"] - L0["solute"]) < 0.01 * L0["solute"]

@@ -142,6 +142,23 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
+def aggregate(ms_local, units_local, dist=None, device=None):
+    """Whole-job figure over ranks: the slowest rank's time and the sum of
+    all ranks' units (replicas: each rank runs its own domain).  Returns
+    (ms_max, units_total, value = units_total / ms_max in units per ms)."""
+    import torch
+
+    t = torch.tensor([float(ms_local), float(units_local)], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized():
+        tm = t[:1].clone()
+        tu = t[1:].clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tu, op=dist.ReduceOp.SUM)
+        t = torch.cat([tm, tu])
+    ms_max, units = float(t[0]), float(t[1])
+    return ms_max, units, units / ms_max
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle timing
 # ---------------------------------------------------------------------------
@@ -382,11 +399,8 @@ def main():
     barrier()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * fluid * K / (ms_max * 1e-3) / 1e6
+    ms_max, units, per_ms = aggregate(ms, fluid * K, dist, device="cuda")
+    value = per_ms * 1e3 / 1e6  # fluid-cell updates per second / 1e6
     sim.check()
 
     # per-kernel durations, CUDA events on the launching stream (no graphs)

@@ -279,3 +279,50 @@ def case_batch(n: int = 256, L_min: int = 32, L_max: int = 96, seed: int = 2310,
         out.append((p, mask, {}))
         meta.append(dict(L=L, porosity=float((mask == 0).mean()), Pe=Pe, Da=Da))
     return out, meta
+
+
+def case_rect_2d(config: str = "A", peda: float = 1.0, scheme: str = "new", a: float = 100.0, b: float = 80.0,
+                 D: float = 0.08, rest_fraction: float = -1.0, magic: float = -1.0, c0: float = 1.0,
+                 precision: str = "fp64"):
+    """2D reaction-diffusion verification rectangle (D2Q5, no flow): constant
+    c0 on the left edge, zero gradient on the right and bottom edges, the
+    reactive wall (c_eq = 0, k_r from PeDa = k_r b_e / D) on top.  Config A
+    is aligned with the grid, config B rotated by 45 degrees.
+
+    Lattice placement (wet-node boundaries): the Dirichlet cells lie on
+    xi = 0 and the reactive cells on eta = b_e, the inert bounce-back walls
+    half a cell beyond the last fluid cells, so the effective rectangle is
+    a_e = a + 1/2 by b_e = b + 1/2.  Returns (params, mask, init, geom) where
+    geom = dict(xi, eta, a_e, b_e, fluid) maps every cell to the rectangle's
+    frame for evaluating the analytical solution."""
+    ae, be = a + 0.5, b + 0.5
+    if config == "A":
+        nx, ny = int(a) + 2, int(b) + 1
+        yy, xx = np.mgrid[0:ny, 0:nx].astype(np.float64)
+        xi, eta = xx, yy + 0.5
+        mask = np.full((ny, nx), REACTIVE, np.uint8)
+        fluid = (xx >= 1) & (xx <= a) & (yy <= b - 1)
+        mask[fluid] = FLUID
+        mask[:, 0] = DIRICHLET
+        inert = (mask == REACTIVE) & ~(yy == b)
+    else:
+        n = int(math.ceil((ae + be) / math.sqrt(2.0))) + 6
+        nx = ny = n
+        yy, xx = np.mgrid[0:ny, 0:nx].astype(np.float64)
+        c = (n - 1) / 2.0
+        # rectangle centre at the grid centre; xi along (1,1)/sqrt2, eta along (-1,1)/sqrt2
+        xi = ((xx - c) + (yy - c)) / math.sqrt(2.0) + ae / 2.0
+        eta = (-(xx - c) + (yy - c)) / math.sqrt(2.0) + be / 2.0
+        fluid = (xi > 0) & (xi < ae) & (eta > 0) & (eta < be)
+        mask = np.full((ny, nx), REACTIVE, np.uint8)
+        mask[fluid] = FLUID
+        mask[(~fluid) & (xi <= 0)] = DIRICHLET
+        inert = (mask == REACTIVE) & ~(eta >= be)
+    k_r = peda * D / be
+    kf = np.where(inert, 0.0, k_r)[None]
+    tau = 0.5 + D / lattice_cs2(5, 2, rest_fraction)
+    p = dict(dim=2, nx=nx, ny=ny, nz=1, flow_q=0, solute_q=5, bc=("wall", "wall", "periodic"), tau_solute=tau,
+             magic_solute=magic, rest_fraction=rest_fraction, k_r=k_r, c_eq=0.0, c_dirichlet=c0, c_init=c0,
+             molar_volume=1.0, scheme=scheme, precision=precision)
+    geom = dict(xi=xi[None], eta=eta[None], a_e=ae, b_e=be, fluid=fluid[None])
+    return p, mask[None], dict(k_field=kf), geom

@@ -45,6 +45,8 @@ def args_():
     ap.add_argument("--pack-n", type=int, default=512, help="edge of the sphere-pack case")
     ap.add_argument("--case", choices=["channel", "spherepack", "batch", "adjoint"], default="channel",
                     help="channel: the headline workload; spherepack: 512^3 precipitation with phase change")
+    ap.add_argument("--sweep", choices=["dense", "staged", "list"], default="dense",
+                    help="fluid-cell sweep of the library (LBRBC_FLUID_SWEEP)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
@@ -137,7 +139,7 @@ def ncu_traffic(kernel_src_hash):
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("engine.cuh", "lattice.cuh"):
+    for f in ("engine.cuh", "lattice.cuh", "staged.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2306_10794_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -377,6 +379,7 @@ def main():
     if dist:
         dist.barrier()
     p, mask, extra, name = workload(a)
+    os.environ["LBRBC_FLUID_SWEEP"] = a.sweep
     K, W = max(1, a.steps), max(3, a.warmup)
     stream = torch.cuda.current_stream()
     sim = lbrbc.Sim(p, mask, **extra)
@@ -466,11 +469,14 @@ def main():
             "dtype": "f32" if a.precision == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": name, "grid": list(mask.shape[::-1]), "fluid_cells": fluid,
                        "wet_boundary_cells": info["boundary_cells"], "parallelism": "replicas" if world > 1 else "1gpu",
+                       "fluid_sweep": a.sweep,
                        "l2_policy": "no flush: populations %.2f GB resident > L2 %.0f MB" % (
                            (26 * (4 if a.precision == "fp32" else 8) * mask.size) / 1e9, L2_BYTES / 1e6)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_fluid (fluid-cell stream-collide, D3Q19 + D3Q7)",
+                         "kernel": "%s (fluid-cell stream-collide, D3Q19 + D3Q7)" % (
+                             "k_fluid_staged" if a.sweep == "staged" else "k_fluid_list" if a.sweep == "list"
+                             else "k_fluid"),
                          "bytes_per_launch": bytes_launch, "ms_per_launch": kms[0], "peak_kind": peak_kind,
                          "traffic_source": traffic_src, "kernel_source_sha256": khash,
                          "step_algorithmic_gbs": step_gbs},

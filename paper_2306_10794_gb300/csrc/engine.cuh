@@ -38,7 +38,9 @@ namespace lbrbc {
 enum : uint32_t { CLS_FLUID = 0, CLS_BOUND = 1, CLS_SOLID = 2 };
 enum : uint8_t { KIND_FLUID = 0, KIND_REACTIVE = 1, KIND_DIRICHLET = 2, KIND_OUTSIDE = 3 };
 enum : int { EV_DISSOLVE = 1, EV_PRECIPITATE = 2 };
-enum : int { ERR_NUMERIC = 1, ERR_OVERFLOW = 2 };
+enum : int { ERR_NUMERIC = 1, ERR_OVERFLOW = 2, ERR_TIMEOUT = 4 };
+// fluid sweep: dense grid, compacted fluid list, or staged row tiles
+enum : int { SWEEP_DENSE = 0, SWEEP_LIST = 1, SWEEP_STAGED = 2 };
 
 // node word of a fluid cell: bits 0-1 class, bits FBIT.. "flow source
 // x - e_i is not fluid" for i = 1..QF-1, bits GBIT.. "solute source
@@ -176,6 +178,9 @@ struct Dev {
     int cap_fl;
     int* nfl;
     uint32_t* fl_xyz;
+    // staged sweep: one flag per row tile (1 = the tile has a fluid cell)
+    int ntiles;
+    uint8_t* tile_on;
     // adjoint recomputation tape (null in ordinary steps): fluid velocity
     // per cell (3 floats) and the streamed h_obar of each reactive link
     float* tape_u;
@@ -281,6 +286,10 @@ __device__ __forceinline__ void collide_solute(T (&g)[L::Q], T C, T ux, T uy, T 
     }
 }
 
+}  // namespace lbrbc
+#include "pairs.cuh"
+namespace lbrbc {
+
 // ---------------------------------------------------------------------------
 // Fluid cells: stream (read side), boundary rules, moments, collide, write.
 // Element indices are 32-bit (checked at creation: Q * NP < 2^32), all loads
@@ -342,41 +351,61 @@ __device__ __forceinline__ void st_pop(T* p, T v) {
 #endif
 }
 
-// One fluid cell (x, y, z) of one step; shared by the single-domain and the
-// batched sweeps.
+// Where a fluid cell's pre-collision populations come from.  GlobalSrc reads
+// the AA slot (read_slot) directly; the staged sweep reads the plain slots
+// from shared memory and only the swapped slots of inactive sources from HBM.
 template <typename T, class LF, class LG, bool ODD>
-__device__ __forceinline__ void fluid_cell(const Dev<T>& a, const Phys& p, const PhysT<T>& q, int x, int y, int z) {
+struct GlobalSrc {
+    const T* __restrict__ F;
+    const T* __restrict__ G;
+    uint32_t id, NP;
+    Nbr32 d;
+    __device__ __forceinline__ bool general() const { return false; }
+    __device__ __forceinline__ T f(int i, bool inactive) const {
+        return ld_pop(F + read_slot<LF, ODD>(id, d, NP, i, inactive));
+    }
+    __device__ __forceinline__ T g(int i, bool inactive) const {
+        return ld_pop(G + read_slot<LG, ODD>(id, d, NP, i, inactive));
+    }
+};
+
+// One fluid cell (x, y, z) of one step with node word w; shared by the
+// single-domain, staged and batched sweeps.
+template <typename T, class LF, class LG, bool ODD, class Src>
+__device__ __forceinline__ void fluid_cell_src(const Dev<T>& a, const Phys& p, const PhysT<T>& q, int x, int y, int z,
+                                               uint32_t id, uint32_t w, const Nbr32& d, const Src& src) {
     constexpr int QF = LF::Q, QG = LG::Q;
     const Geo& g = a.geo;
-    const uint32_t id = (uint32_t)g.idx(x, y, z);
-    const uint32_t w = a.nw[id];
-    if ((w & 3u) != CLS_FLUID) return;
-    const Nbr32 d = nbr32(g, x, y, z);
     const uint32_t NP = (uint32_t)g.NP;
     T* __restrict__ F = a.F;
     T* __restrict__ G = a.G;
     const bool inlet = g.open_x && x == 0;
     const bool outlet = g.open_x && x == g.nx - 1;
-    const bool plain = (w >> FBIT) == 0u && !inlet && !outlet;
+    const bool plain = (w >> FBIT) == 0u && !inlet && !outlet && !src.general();
 
+    // Warps whose cells all read the plain slots take a path with no
+    // per-direction tests; the others pick, per direction, the plain slot or
+    // the swapped one of an inactive source.
     T f[QF > 0 ? QF : 1];
     T gg[QG];
-    if (plain) {
+    if (__all_sync(__activemask(), plain)) {
 #pragma unroll
-        for (int i = 0; i < QF; ++i) f[i] = ld_pop(F + read_slot<LF, ODD>(id, d, NP, i, false));
+        for (int i = 0; i < QF; ++i) f[i] = src.f(i, false);
 #pragma unroll
-        for (int i = 0; i < QG; ++i) gg[i] = ld_pop(G + read_slot<LG, ODD>(id, d, NP, i, false));
+        for (int i = 0; i < QG; ++i) gg[i] = src.g(i, false);
     } else {
 #pragma unroll
         for (int i = 0; i < QF; ++i) {
             const bool wall = i > 0 && ((w >> (FBIT + i - 1)) & 1u);
-            f[i] = ld_pop(F + read_slot<LF, ODD>(id, d, NP, i, wall));
+            f[i] = src.f(i, wall);
         }
 #pragma unroll
         for (int i = 0; i < QG; ++i) {
             const bool wall = i > 0 && ((w >> (GBIT + i - 1)) & 1u);
-            gg[i] = ld_pop(G + read_slot<LG, ODD>(id, d, NP, i, wall));
+            gg[i] = src.g(i, wall);
         }
+    }
+    if (!plain) {
         const int face = y + g.ny * z;
         if constexpr (QF > 0) {
             if (inlet) {
@@ -413,34 +442,18 @@ __device__ __forceinline__ void fluid_cell(const Dev<T>& a, const Phys& p, const
 
     T ux = T(0), uy = T(0), uz = T(0), rho = T(1);
     if constexpr (QF > 0) {
-        T s = T(0), jx = T(0), jy = T(0), jz = T(0);
-#pragma unroll
-        for (int i = 0; i < QF; ++i) {
-            s += f[i];
-            if (LF::cx(i)) jx += T(LF::cx(i)) * f[i];
-            if (LF::cy(i)) jy += T(LF::cy(i)) * f[i];
-            if (LF::cz(i)) jz += T(LF::cz(i)) * f[i];
-        }
-        rho = T(1) + s;
-        const T inv = T(1) / rho;
-        ux = jx * inv;
-        uy = jy * inv;
-        uz = jz * inv;
-        collide_flow<LF, T>(reinterpret_cast<T(&)[QF]>(f), rho, ux, uy, uz, p, q);
+        flow_pairs<LF, T>(reinterpret_cast<T(&)[QF]>(f), rho, ux, uy, uz, p, q);
 #pragma unroll
         for (int i = 0; i < QF; ++i) st_pop(F + write_slot<LF, ODD>(id, d, NP, i), f[i]);
     }
-    T sc = T(0);
-#pragma unroll
-    for (int i = 0; i < QG; ++i) sc += gg[i];
-    const T C = q.cref + sc;
+    T C;
+    solute_pairs<LG, T>(gg, C, ux, uy, uz, p, q);
     if (!(rho > T(0)) || !isfinite(C)) *a.err |= ERR_NUMERIC;
     if (a.tape_u) {
         a.tape_u[3 * (size_t)id] = (float)ux;
         a.tape_u[3 * (size_t)id + 1] = (float)uy;
         a.tape_u[3 * (size_t)id + 2] = (float)uz;
     }
-    collide_solute<LG, T>(gg, C, ux, uy, uz, p, q);
 #pragma unroll
     for (int i = 0; i < QG; ++i) st_pop(G + write_slot<LG, ODD>(id, d, NP, i), gg[i]);
     if (outlet) {
@@ -453,7 +466,18 @@ __device__ __forceinline__ void fluid_cell(const Dev<T>& a, const Phys& p, const
 }
 
 template <typename T, class LF, class LG, bool ODD>
-__global__ void __launch_bounds__(FLUID_BLOCK) k_fluid(const Dev<T> a, const Phys p, const PhysT<T> q) {
+__device__ __forceinline__ void fluid_cell(const Dev<T>& a, const Phys& p, const PhysT<T>& q, int x, int y, int z) {
+    const Geo& g = a.geo;
+    const uint32_t id = (uint32_t)g.idx(x, y, z);
+    const uint32_t w = a.nw[id];
+    if ((w & 3u) != CLS_FLUID) return;
+    const Nbr32 d = nbr32(g, x, y, z);
+    const GlobalSrc<T, LF, LG, ODD> src{a.F, a.G, id, (uint32_t)g.NP, d};
+    fluid_cell_src<T, LF, LG, ODD>(a, p, q, x, y, z, id, w, d, src);
+}
+
+template <typename T, class LF, class LG, bool ODD>
+__global__ void __launch_bounds__(FLUID_BLOCK, sizeof(T) == 4 ? 8 : 5) k_fluid(const Dev<T> a, const Phys p, const PhysT<T> q) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= a.geo.nx) return;
     fluid_cell<T, LF, LG, ODD>(a, p, q, x, blockIdx.y, blockIdx.z);
@@ -1415,6 +1439,7 @@ __global__ void k_sum_partials(const double* bacc, int nblocks, const double* ac
 }
 
 }  // namespace lbrbc
+#include "staged.cuh"
 #include "adjoint.cuh"
 namespace lbrbc {
 
@@ -1545,10 +1570,12 @@ class Engine final : public ISim {
         d_.cap_b = grow(nb0);
         d_.cap_f = grow(nf0);
         d_.cap_e = (int)std::min<long long>(ncell_ + 64, std::max<long long>(1 << 16, ncell_ / 64));
-        // Sweep over the dense grid (default) or over a compacted fluid-cell
-        // list (LBRBC_FLUID_SWEEP=list, or a batch schedule).  Measured on
-        // GB300 sphere packs the list is slower: a warp's 32 list cells span
-        // several rows, so every population load touches more lines.
+        // Sweep over the dense grid (default), over a compacted fluid-cell
+        // list (LBRBC_FLUID_SWEEP=list, or a batch schedule) or over staged
+        // row tiles (LBRBC_FLUID_SWEEP=staged).  Measured on GB300 both
+        // alternatives are slower: a warp's 32 list cells span several rows,
+        // so every population load touches more lines; the staged tiles
+        // leave fewer warps to issue an issue-bound cell update.
         {
             long long active = 0;
             for (int z = 0; z < g.nz; ++z)
@@ -1562,12 +1589,15 @@ class Engine final : public ISim {
             lane_eff_ = active ? (double)nfluid / (32.0 * active) : 1.0;
             const bool fits = g.nx <= 2048 && g.ny <= 2048 && g.nz <= 1024;
             const char* env = getenv("LBRBC_FLUID_SWEEP");
-            int want = 0;
-            if (env && !strcmp(env, "list")) want = 1;
-            if (env && !strcmp(env, "dense")) want = 0;
-            if (force_list_) want = 1;
+            int want = SWEEP_DENSE;
+            if (env && !strcmp(env, "list")) want = SWEEP_LIST;
+            if (env && !strcmp(env, "dense")) want = SWEEP_DENSE;
+            if (env && !strcmp(env, "staged")) want = SWEEP_STAGED;
+            if (force_list_) want = SWEEP_LIST;
             // (the list sweep is not combined with phase change)
-            d_.use_fl = want && fits && !P.phase_change;
+            if (want == SWEEP_LIST && !(fits && !P.phase_change)) want = SWEEP_DENSE;
+            sweep_ = want;
+            d_.use_fl = want == SWEEP_LIST;
             d_.cap_fl = (int)std::min<long long>(ncell_, std::max<long long>(2 * nfluid, nfluid + ncell_ / 8) + 1024);
         }
         d_.cap_log = P.event_log_capacity > 0 ? P.event_log_capacity : 0;
@@ -1594,6 +1624,18 @@ class Engine final : public ISim {
         LB_CUDA(dalloc(&d_.f_idx, (size_t)d_.cap_f));
         LB_CUDA(dalloc(&d_.f_share, (size_t)(QG - 1) * d_.cap_f));
         LB_CUDA(dalloc(&d_.nfl, 1));
+        d_.ntiles = 0;
+        d_.tile_on = nullptr;
+        if (sweep_ == SWEEP_STAGED) {
+            const long long nt = (long long)((g.nx + TILE_X - 1) / TILE_X) * g.ny * g.nz;
+            if (nt >= (1LL << 31)) {
+                err = "too many row tiles for the staged sweep";
+                return 1;
+            }
+            d_.ntiles = (int)nt;
+            LB_CUDA(dalloc(&d_.tile_on, (size_t)nt));
+            if (setup_staged(err)) return 2;
+        }
         if (d_.use_fl) LB_CUDA(dalloc(&d_.fl_xyz, (size_t)d_.cap_fl));
         else d_.fl_xyz = nullptr;
         LB_CUDA(cudaMemset(d_.nfl, 0, sizeof(int)));
@@ -1620,6 +1662,9 @@ class Engine final : public ISim {
         LB_CUDA(dalloc(&d_.err, 1));
         LB_CUDA(dalloc(&d_.blk, (size_t)nchunks_ + 1));
         LB_CUDA(cudaStreamCreateWithFlags(&own_, cudaStreamNonBlocking));
+        LB_CUDA(cudaStreamCreateWithFlags(&aux_, cudaStreamNonBlocking));
+        LB_CUDA(cudaEventCreateWithFlags(&fork_, cudaEventDisableTiming));
+        LB_CUDA(cudaEventCreateWithFlags(&join_, cudaEventDisableTiming));
 
         // uploads
         std::vector<double> phi(NP, 0.0);
@@ -1877,6 +1922,10 @@ class Engine final : public ISim {
         if (herr & ERR_NUMERIC) {
             err = "non-finite concentration or non-positive density encountered";
             return 3;
+        }
+        if (herr & ERR_TIMEOUT) {
+            err = "a bounded device wait of the staged sweep gave up";
+            return 4;
         }
         return 0;
     }
@@ -2141,6 +2190,7 @@ class Engine final : public ISim {
     // Reclassification and list rebuild (force = 1 at creation: unconditional).
     int rebuild(cudaStream_t st, int lastodd, int force, std::string& err) {
         k_reclassify<T, LF, LG><<<grid_for(ncell_, 256), 256, 0, st>>>(d_, ph_, lastodd, force);
+        if (sweep_ == SWEEP_STAGED) k_tile_flags<T><<<grid_for((long long)d_.ntiles * 32, 256), 256, 0, st>>>(d_, force);
         for (int which = 0; which < (d_.use_fl ? 3 : 2); ++which) {
             k_count<T, LG><<<nchunks_, 256, 0, st>>>(d_, which, force);
             k_scan<T><<<1, 1024, 0, st>>>(d_, nchunks_, which, force);
@@ -2158,7 +2208,25 @@ class Engine final : public ISim {
         const Geo& g = d_.geo;
         dim3 grid((g.nx + FLUID_BLOCK - 1) / FLUID_BLOCK, g.ny, g.nz);
         if (ev) LB_CUDA(cudaEventRecord(ev[0], st));
-        if (d_.use_fl) {
+        // Without per-group timing the boundary list and the fluid ends run
+        // on a second stream beside the fluid sweep: the three kernels touch
+        // disjoint population slots (each slot is read and written by one
+        // cell per step), and the fluid ends depend only on the boundary list.
+        const bool fork = ev == nullptr;
+        if (fork) {
+            LB_CUDA(cudaEventRecord(fork_, st));
+            LB_CUDA(cudaStreamWaitEvent(aux_, fork_, 0));
+            const int lg = list_grid(d_.cap_b);
+            if (odd) k_bound<T, LG, true><<<lg, LIST_BLOCK, 0, aux_>>>(d_, ph_, pt_);
+            else k_bound<T, LG, false><<<lg, LIST_BLOCK, 0, aux_>>>(d_, ph_, pt_);
+            k_fend<T, LG><<<list_grid(d_.cap_f), LIST_BLOCK, 0, aux_>>>(d_, ph_);
+            LB_CUDA(cudaEventRecord(join_, aux_));
+        }
+        if (sweep_ == SWEEP_STAGED) {
+            const size_t sm = (size_t)staged_stages<T>() * staged_stage_bytes<T, LF, LG>();
+            if (odd) k_fluid_staged<T, LF, LG, true><<<sgrid_, TILE_X, sm, st>>>(d_, ph_, pt_);
+            else k_fluid_staged<T, LF, LG, false><<<sgrid_, TILE_X, sm, st>>>(d_, ph_, pt_);
+        } else if (d_.use_fl) {
             const int gl = (int)((d_.cap_fl + FLUID_BLOCK - 1) / FLUID_BLOCK);
             if (odd) k_fluid_list<T, LF, LG, true><<<gl, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_);
             else k_fluid_list<T, LF, LG, false><<<gl, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_);
@@ -2166,13 +2234,17 @@ class Engine final : public ISim {
             if (odd) k_fluid<T, LF, LG, true><<<grid, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_);
             else k_fluid<T, LF, LG, false><<<grid, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_);
         }
-        if (ev) LB_CUDA(cudaEventRecord(ev[1], st));
-        const int lg = list_grid(d_.cap_b);
-        if (odd) k_bound<T, LG, true><<<lg, LIST_BLOCK, 0, st>>>(d_, ph_, pt_);
-        else k_bound<T, LG, false><<<lg, LIST_BLOCK, 0, st>>>(d_, ph_, pt_);
-        if (ev) LB_CUDA(cudaEventRecord(ev[2], st));
-        k_fend<T, LG><<<list_grid(d_.cap_f), LIST_BLOCK, 0, st>>>(d_, ph_);
-        if (ev) LB_CUDA(cudaEventRecord(ev[3], st));
+        if (fork) {
+            LB_CUDA(cudaStreamWaitEvent(st, join_, 0));
+        } else {
+            LB_CUDA(cudaEventRecord(ev[1], st));
+            const int lg = list_grid(d_.cap_b);
+            if (odd) k_bound<T, LG, true><<<lg, LIST_BLOCK, 0, st>>>(d_, ph_, pt_);
+            else k_bound<T, LG, false><<<lg, LIST_BLOCK, 0, st>>>(d_, ph_, pt_);
+            LB_CUDA(cudaEventRecord(ev[2], st));
+            k_fend<T, LG><<<list_grid(d_.cap_f), LIST_BLOCK, 0, st>>>(d_, ph_);
+            LB_CUDA(cudaEventRecord(ev[3], st));
+        }
         if (ph_.phase_change) {
             const int eg = 152 * 2;
             const int lo = odd ? 1 : 0;
@@ -2221,6 +2293,38 @@ class Engine final : public ISim {
     }
 
    private:
+    // Shared memory and persistent grid of the staged sweep: as many CTAs as
+    // fit on the device at once (never more than there are tiles).
+    int setup_staged(std::string& err) {
+        const size_t sm = (size_t)staged_stages<T>() * staged_stage_bytes<T, LF, LG>();
+        int occ = 64;
+        int dev = 0, nsm = 0;
+        LB_CUDA(cudaGetDevice(&dev));
+        LB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        auto occ_of = [&](auto kern) -> int {
+            int o = 0;
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return -1;
+            // the persistent grid assumes every CTA of the occupancy
+            // estimate is resident: ask for the largest shared-memory carveout
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+                return -1;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, TILE_X, sm) != cudaSuccess) return -1;
+            return o;
+        };
+        const int o[2] = {occ_of(k_fluid_staged<T, LF, LG, false>), occ_of(k_fluid_staged<T, LF, LG, true>)};
+        for (int k = 0; k < 2; ++k) {
+            if (o[k] < 0) {
+                err = std::string("staged sweep setup: ") + cudaGetErrorString(cudaGetLastError());
+                return 2;
+            }
+            occ = std::min(occ, o[k]);
+        }
+        occ = std::max(1, occ);
+        sgrid_ = (int)std::max<long long>(1, std::min<long long>((long long)nsm * occ, d_.ntiles));
+        return 0;
+    }
+
     static int list_grid(int cap) {
         return (int)std::max(1, std::min(152 * 8, (cap + LIST_BLOCK - 1) / LIST_BLOCK));
     }
@@ -2269,6 +2373,11 @@ class Engine final : public ISim {
         allocs_.clear();
         if (own_) cudaStreamDestroy(own_);
         own_ = nullptr;
+        if (aux_) cudaStreamDestroy(aux_);
+        aux_ = nullptr;
+        if (fork_) cudaEventDestroy(fork_);
+        if (join_) cudaEventDestroy(join_);
+        fork_ = join_ = nullptr;
     }
 
     lbrbc_params prm_{};
@@ -2280,7 +2389,10 @@ class Engine final : public ISim {
     int nbacc_ = 0;
     int lastodd_ = 1;
     int64_t steps_ = 0;
-    cudaStream_t own_ = nullptr, last_stream_ = nullptr;
+    cudaStream_t own_ = nullptr, last_stream_ = nullptr, aux_ = nullptr;
+    cudaEvent_t fork_ = nullptr, join_ = nullptr;
+    int sweep_ = SWEEP_DENSE;
+    int sgrid_ = 1;
     cudaGraphExec_t g_even_{}, g_odd_{}, g_pair_{};
     bool graphs_ = false;
     bool batched_ = false;

@@ -19,9 +19,10 @@ pytestmark = pytest.mark.gpu
 TOL64 = 1e-11
 
 
-@pytest.fixture(params=["dense", "list"])
+@pytest.fixture(params=["dense", "list", "staged"])
 def sweep(request, monkeypatch):
-    # the fluid sweep runs over the dense grid or over the compacted fluid list
+    # the fluid sweep runs over the dense grid, the compacted fluid list or
+    # staged row tiles
     monkeypatch.setenv("LBRBC_FLUID_SWEEP", request.param)
     return request.param
 
@@ -78,7 +79,7 @@ def test_sphere_pack_periodic_fp64(steps, magic_f, magic_g, sweep):
 
 
 @pytest.mark.parametrize("scheme", ["new", "verhaeghe", "patel_ju", "anti_bb"])
-def test_schemes_walls_and_dirichlet_fp64(scheme):
+def test_schemes_walls_and_dirichlet_fp64(scheme, sweep):
     # non-periodic y/z walls, a Dirichlet slab and a reactive pack, k field
     shape = (11, 19, 45)
     mask = pack(shape, 3, periodic=(True, False, False), por=0.6)
@@ -102,7 +103,7 @@ def test_open_channel_fp64(sweep):
 
 
 @pytest.mark.parametrize("case", ["d2q9_solute", "d2q5_solute", "d2q9_d2q5_flow"])
-def test_2d_fp64(case):
+def test_2d_fp64(case, sweep):
     if case == "d2q9_solute":
         p, mask, _ = workloads.case_wall_2d(nx=133, ny=40, tau=0.8, solute_q=9)
     elif case == "d2q5_solute":
@@ -136,10 +137,13 @@ def test_fp32_relative_l2(sweep):
 
 
 @pytest.mark.parametrize("c_init,phi_solid,kind", [(3.0, 1.0, 2), (0.0, 0.03, 1)])
-def test_phase_change_events_identical_fp64(c_init, phi_solid, kind):
+@pytest.mark.parametrize("mode", ["dense", "staged"])
+def test_phase_change_events_identical_fp64(c_init, phi_solid, kind, mode, monkeypatch):
     # Events are threshold decisions on FP64 values that differ from the
     # oracle's by rounding only; identity holds unless a cell lands within
-    # rounding of a threshold.  The default (dense) sweep is checked here.
+    # rounding of a threshold.  The tile flags of the staged sweep follow
+    # the reclassified cells.
+    monkeypatch.setenv("LBRBC_FLUID_SWEEP", mode)
     shape = (14, 16, 36)
     mask = pack(shape, 7)
     rng = np.random.default_rng(8)

@@ -139,7 +139,7 @@ def ncu_traffic(kernel_src_hash):
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("engine.cuh", "lattice.cuh", "staged.cuh"):
+    for f in ("engine.cuh", "lattice.cuh", "pairs.cuh", "staged.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2306_10794_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

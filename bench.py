@@ -43,10 +43,12 @@ def args_():
     ap.add_argument("--da", type=float, default=1.0)
     ap.add_argument("--size", type=str, default="256x128x128")
     ap.add_argument("--pack-n", type=int, default=512, help="edge of the sphere-pack case")
-    ap.add_argument("--case", choices=["channel", "spherepack", "batch", "adjoint"], default="channel",
+    ap.add_argument("--case", choices=["channel", "spherepack", "batch", "adjoint", "molins"], default="channel",
                     help="channel: the headline workload; spherepack: 512^3 precipitation with phase change")
     ap.add_argument("--sweep", choices=["dense", "staged", "list"], default="dense",
                     help="fluid-cell sweep of the library (LBRBC_FLUID_SWEEP)")
+    ap.add_argument("--molins-cases", type=str, default="4", help="Table 2 cases of --case molins, e.g. 1,2,3,4")
+    ap.add_argument("--scale", type=float, default=1.0, help="resolution of --case molins (1 = the paper's 600x1200)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
@@ -248,6 +250,72 @@ def reference_arm(a):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+# Table 2 of the paper (Sec. 3.3): R_avg in 1e-8 mol/(cm^2 s) per case and
+# scheme, the printed values the molins case is compared with.
+TABLE2 = {1: dict(verhaeghe=4.48, patel_ju=4.66, new=4.64, anti_bb=4.71),
+          2: dict(verhaeghe=4.70, patel_ju=4.70, new=4.70, anti_bb=4.71),
+          3: dict(verhaeghe=75.5, patel_ju=75.9, new=75.8, anti_bb=76.0),
+          4: dict(verhaeghe=8.05, patel_ju=29.1, new=18.5, anti_bb=76.0)}
+
+
+def molins_arm(a):
+    """Reactive disc in a channel flow (Sec. 3.3): every scheme of the
+    chosen Table 2 cases run to a steady R_avg (relative change below 1e-4
+    over a chunk), R_avg from the outlet integral and from the ledger, the
+    paper's value beside it, and the coupled MLUPS of the run."""
+    import numpy as np
+    import torch
+
+    from paper_2306_10794_gb300 import _build, experiments, lbrbc, workloads
+
+    _build.build()
+    stream = torch.cuda.current_stream()
+    rows, cells_steps, t_total = [], 0, 0.0
+    for case in [int(c) for c in a.molins_cases.split(",")]:
+        for scheme in ("verhaeghe", "patel_ju", "new", "anti_bb"):
+            p, mask, init, geom = workloads.case_molins(case, scheme, a.scale, precision=a.precision)
+            s = lbrbc.Sim(p, mask, **init)
+            fluid = s.info()["fluid_cells"]
+            chunk = max(1000, int(250_000 * a.scale * a.scale))
+            cap = 3 * geom["steps_hint"]
+            done, prev, led_prev = 0, None, s.ledger()["reacted"]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ms = 0.0
+            while True:
+                e0.record(stream)
+                s.step(chunk, stream=stream.cuda_stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+                done += chunk
+                u, _, c, _ = s.fields()
+                r = experiments.molins_ravg(u, c, geom)[1]
+                led = s.ledger()["reacted"]
+                r_led = -(led - led_prev) / chunk / (np.pi * geom["d_obj"]) * geom["to_paper"]
+                led_prev = led
+                if prev is not None and abs(r - prev) <= 1e-4 * abs(r) or done >= cap:
+                    break
+                prev = r
+            s.check()
+            s.close()
+            cells_steps += fluid * done
+            t_total += ms * 1e-3
+            rows.append({"case": case, "scheme": scheme, "R_avg": r, "R_avg_ledger": r_led,
+                         "paper": TABLE2[case][scheme], "rel_to_paper": r / TABLE2[case][scheme] - 1.0,
+                         "steps": done, "converged": done < cap, "mlups": fluid * done / (ms * 1e-3) / 1e6})
+    new4 = [x["R_avg"] for x in rows if x["case"] == 4 and x["scheme"] == "new"]
+    line = {"metric": "R_avg of the reactive disc in a channel flow (Table 2)",
+            "value": new4[0] if new4 else rows[0]["R_avg"], "unit": "1e-8 mol/(cm^2 s)", "n_gpus": 1,
+            "steps": int(sum(x["steps"] for x in rows)), "warmup": 0, "higher_is_better": None, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if a.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": "2D reactive disc in a channel, %dx%d cells (scale %.2f of 600x1200), D2Q9 TRT flow "
+                                   "Re=0.6 + D2Q5 TRT solute with rest fraction, cases %s, four k_i schemes"
+                                   % (int(round(1200 * a.scale)), int(round(600 * a.scale)), a.scale, a.molins_cases)},
+            "table": rows, "mlups": cells_steps / t_total / 1e6, "gpu_launches": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def batch_arm(a):
     """256 uneven dissolution domains: autotuned batched launches vs one
     launch (CUDA graph) per domain per step."""
@@ -360,6 +428,8 @@ def main():
         return adjoint_arm(a)
     if a.case == "batch":
         return batch_arm(a)
+    if a.case == "molins":
+        return molins_arm(a)
     import numpy as np
     import torch
 

@@ -17,6 +17,7 @@ Cases (sizes are the arguments' defaults):
   in [r_min, r_max], added until the porosity reaches the target.
 * ``annulus`` -- 2D reactive disk inside a Dirichlet circle.
 * ``lognormal_k`` -- per-voxel rate k_bar exp(sigma Z - sigma^2 / 2).
+* ``case_molins`` -- 2D reactive disc in a channel flow (Sec. 3.3, Table 2).
 """
 from __future__ import annotations
 
@@ -326,3 +327,48 @@ def case_rect_2d(config: str = "A", peda: float = 1.0, scheme: str = "new", a: f
              molar_volume=1.0, scheme=scheme, precision=precision)
     geom = dict(xi=xi[None], eta=eta[None], a_e=ae, b_e=be, fluid=fluid[None])
     return p, mask[None], dict(k_field=kf), geom
+
+
+# Sec. 3.3 / Table 2: (Pe, Da) of the four cases and the rest fraction the
+# paper uses for each Pe.
+MOLINS_CASES = {1: (600.0, 178.0), 2: (600.0, 17800.0), 3: (6.0, 178.0), 4: (6.0, 0.178)}
+MOLINS_J0 = {600.0: 0.99, 6.0: 1.0 / 3.0}
+
+
+def case_molins(case: int = 4, scheme: str = "new", scale: float = 1.0, magic_flow: float = 3.0 / 16.0,
+                magic_solute: float = 0.25, precision: str = "fp32"):
+    """2D reactive disc in a channel flow (Sec. 3.3): channel H x W = 600 x
+    1200 cells at scale 1 (0.05 cm x 0.1 cm), disc of diameter 240 cells
+    (0.02 cm) at the centre, plug inlet U = 0.001 / scale, rho = 1 outlet,
+    bounce-back channel walls; D2Q9 TRT flow at Re = U H / nu = 0.6
+    (tau = 3.5 at every scale), D2Q5 TRT solute with the paper's rest
+    fraction, Pe = U H / D, Da = k_r / U (Eq. PeDa), c_in = c_init = 1,
+    c_eq = 0 on the disc.  Returns (params, mask, init, geom); geom holds
+    what the average reaction rate of Eq. avgReactionRateMolins needs and
+    the factor from lattice to the paper's unit (1e-8 mol / (cm^2 s)) for
+    c_in = 10 mol/m^3 and u_in = 0.12 cm/s."""
+    Pe, Da = MOLINS_CASES[case]
+    H, W = int(round(600 * scale)), int(round(1200 * scale))
+    d_obj = 240.0 * scale
+    U = 0.001 / scale
+    Re = 0.6
+    nu = U * H / Re
+    tau_f = 3.0 * nu + 0.5
+    J0 = MOLINS_J0[Pe]
+    D = U * H / Pe
+    cs2 = lattice_cs2(5, 2, J0)
+    tau_g = 0.5 + D / cs2
+    yy, xx = np.mgrid[0:H, 0:W].astype(np.float64)
+    cx, cy = (W - 1) / 2.0, (H - 1) / 2.0
+    disc = (xx - cx) ** 2 + (yy - cy) ** 2 <= (0.5 * d_obj) ** 2
+    mask = np.where(disc, REACTIVE, FLUID).astype(np.uint8)[None]
+    p = dict(dim=2, nx=W, ny=H, nz=1, flow_q=9, solute_q=5, bc=("open", "wall", "periodic"), tau_flow=tau_f,
+             magic_flow=magic_flow, tau_solute=tau_g, magic_solute=magic_solute, rest_fraction=J0, k_r=Da * U,
+             c_eq=0.0, c_init=1.0, c_inlet=1.0, u_inlet=U, rho_outlet=1.0, molar_volume=1.0, scheme=scheme,
+             precision=precision)
+    # lattice concentration 1 = 10 mol/m^3 = 1e-5 mol/cm^3; lattice velocity
+    # U = 0.12 cm/s; result in 1e-8 mol/(cm^2 s)
+    to_paper = 1e-5 * (0.12 / U) / 1e-8
+    geom = dict(H=H, W=W, d_obj=d_obj, U=U, c_in=1.0, Pe=Pe, Da=Da, to_paper=to_paper,
+                steps_hint=int(4.0e6 * scale * scale))
+    return p, mask, {}, geom

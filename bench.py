@@ -124,9 +124,15 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def ncu_traffic(kernel_src_hash):
+def workload_key(a):
+    """Identifies the workload an ncu summary was taken on."""
+    return "%s-%s-%s-theta%g-pe%g-da%g-%s" % (a.case, a.size, a.precision, a.theta, a.pe, a.da, a.sweep)
+
+
+def ncu_traffic(kernel_src_hash, wkey):
     """DRAM bytes per launch of the fluid kernel from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
+    if it was taken on the current kernel source and on this workload (else
+    None)."""
     path = os.path.join(ROOT, "profiles", "k_fluid_channel.md")
     try:
         txt = open(path).read()
@@ -134,9 +140,10 @@ def ncu_traffic(kernel_src_hash):
         return None, None
     m = re.search(r"source_sha256:\s*([0-9a-f]+)", txt)
     t = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
-    if not m or not t or m.group(1) != kernel_src_hash:
+    w = re.search(r"workload_key:\s*(\S+)", txt)
+    if not m or not t or not w or m.group(1) != kernel_src_hash or w.group(1) != wkey:
         return None, None
-    return float(t.group(1)), path
+    return float(t.group(1)), os.path.relpath(path, ROOT)
 
 
 def kernel_hash():
@@ -484,7 +491,7 @@ def main():
     peak, peak_kind = measured_peak()
     achieved = bytes_launch / (kms[0] * 1e-3) / 1e9
     khash = kernel_hash()
-    traffic, traffic_src = ncu_traffic(khash)
+    traffic, traffic_src = ncu_traffic(khash, workload_key(a))
     step_gbs = bytes_launch / (ms_max / K * 1e-3) / 1e9
 
     # accuracy of this precision against the FP64 path (outside the timed region)

@@ -18,6 +18,8 @@ Cases (sizes are the arguments' defaults):
 * ``annulus`` -- 2D reactive disk inside a Dirichlet circle.
 * ``lognormal_k`` -- per-voxel rate k_bar exp(sigma Z - sigma^2 / 2).
 * ``case_molins`` -- 2D reactive disc in a channel flow (Sec. 3.3, Table 2).
+* ``case_grain_2d`` -- 2D grain growth by precipitation from a star-shaped
+  seed inside a circle of fixed concentration (Sec. 3.2).
 """
 from __future__ import annotations
 
@@ -372,3 +374,31 @@ def case_molins(case: int = 4, scheme: str = "new", scale: float = 1.0, magic_fl
     geom = dict(H=H, W=W, d_obj=d_obj, U=U, c_in=1.0, Pe=Pe, Da=Da, to_paper=to_paper,
                 steps_hint=int(4.0e6 * scale * scale))
     return p, mask, {}, geom
+
+
+def case_grain_2d(angle_deg: float = 0.0, scheme: str = "new", n: int = 300, k_r: float = 0.0014,
+                  tau: float = 1.0, molar_volume: float = 0.2, c_init: float = 1.0, precision: str = "fp32"):
+    """Grain growth during precipitation (Sec. 3.2): an n x n square with
+    Dirichlet cells (C = 1) outside the inscribed circle of diameter n, a
+    seed in the centre bounded by the curve r(s) = [0.1 + 0.02 cos(8 pi s)] n
+    at polar angle 2 pi s, turned clockwise by angle_deg, reacting with
+    C_eq = 0 and k_r (precipitation: the seed grows), pure diffusion on D2Q5
+    with BGK (tau), phase change on.  Returns (params, mask, init, geom);
+    geom holds the centre, the seed mask and the cells inside the circle."""
+    yy, xx = np.mgrid[0:n, 0:n].astype(np.float64)
+    c = (n - 1) / 2.0
+    dx, dy = xx - c, yy - c
+    r = np.hypot(dx, dy)
+    # polar angle in the seed's own frame: a clockwise turn by angle_deg shows
+    # the seed's feature at angle t at grid angle t - angle_deg
+    t = np.arctan2(dy, dx) + math.radians(angle_deg)
+    seed = r <= (0.1 + 0.02 * np.cos(4.0 * t)) * n
+    outside = r > 0.5 * n - 0.5
+    mask = np.full((n, n), FLUID, np.uint8)
+    mask[seed] = REACTIVE
+    mask[outside] = DIRICHLET
+    p = dict(dim=2, nx=n, ny=n, nz=1, flow_q=0, solute_q=5, bc=("wall", "wall", "periodic"), tau_solute=tau,
+             magic_solute=-1.0, rest_fraction=-1.0, k_r=k_r, c_eq=0.0, c_dirichlet=1.0, c_init=c_init,
+             molar_volume=molar_volume, phase_change=1, scheme=scheme, precision=precision)
+    geom = dict(centre=(c, c), seed=seed[None], inside=(~outside)[None])
+    return p, mask[None], {}, geom

@@ -173,3 +173,21 @@ def test_mass_invariant_gpu_fp64():
     g.step(150)
     g.check()
     assert abs(inv(g.ledger()) - I0) < 1e-12 * abs(I0)
+
+
+@pytest.mark.parametrize("scheme,angle", [("new", 0.0), ("patel_ju", 19.0)])
+def test_phase_change_2d_grain_fp64(scheme, angle):
+    # 2D precipitation on a star-shaped seed inside a circle of fixed
+    # concentration (the setup of Sec. 3.2 at 61 x 61): identical events,
+    # classes and fields, on aligned and turned seeds
+    p, mask, _, _ = workloads.case_grain_2d(angle, scheme, n=61, k_r=0.02, molar_volume=0.5, precision="fp64")
+    p["event_log_capacity"] = 1 << 16
+    g, o = run_both(p, mask, 200)
+    eo, eg = o.events(), g.events()
+    assert len(eo) > 20 and set(eo[:, 2].tolist()) == {2}
+    key = lambda e: sorted(map(tuple, e.tolist()))
+    assert key(eg) == key(eo)
+    compare64(g, o)
+    lg, lo = g.ledger(), o.ledger()
+    for k in ("solute", "solid_over_vm", "dirichlet_in", "reacted"):
+        assert abs(lg[k] - lo[k]) < 1e-9 * max(1.0, abs(lo[k])), (k, lg[k], lo[k])

@@ -1662,7 +1662,14 @@ class Engine final : public ISim {
         LB_CUDA(dalloc(&d_.err, 1));
         LB_CUDA(dalloc(&d_.blk, (size_t)nchunks_ + 1));
         LB_CUDA(cudaStreamCreateWithFlags(&own_, cudaStreamNonBlocking));
-        LB_CUDA(cudaStreamCreateWithFlags(&aux_, cudaStreamNonBlocking));
+        {
+            // the boundary branch runs beside the fluid sweep; the highest
+            // priority lets its few blocks start first instead of queueing
+            // behind the sweep's
+            int lo = 0, hi = 0;
+            LB_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+            LB_CUDA(cudaStreamCreateWithPriority(&aux_, cudaStreamNonBlocking, hi));
+        }
         LB_CUDA(cudaEventCreateWithFlags(&fork_, cudaEventDisableTiming));
         LB_CUDA(cudaEventCreateWithFlags(&join_, cudaEventDisableTiming));
 

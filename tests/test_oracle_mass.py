@@ -80,3 +80,41 @@ def test_single_dissolution_event_by_hand():
     Q = Vm * (c_init - c_ref[0, 1, 2]) - phi_ref[0, 1, 2]
     paid = phi_ref[0, [1, 1, 0], [1, 3, 2]] - phi[0, [1, 1, 0], [1, 3, 2]]
     assert np.allclose(paid, Q / 3.0, rtol=1e-12)
+
+
+def test_single_precipitation_event_by_hand():
+    """A fluid cell whose phi reaches >= 1 turns solid (Sec. 2.4, reading
+    R5): phi += V_m C, its solute is removed, phi := 1, and the excess goes
+    to its fluid neighbours as concentration, weighted by the new link
+    coefficients (e_o.n)+.  Here the new cell is a bump on a flat wall: the
+    isotropic gradient of the solid indicator at the bump, evaluated by hand
+    with the D2Q9 weights, is 3 * (w_axis (0,-1) + w_diag ((1,-1) + (-1,-1)))
+    = (0, -1/2), so n = (0, 1): the upward link has kappa = 1 and the two
+    sideways links kappa = 0, and the whole excess goes up.  The wall cell
+    below the bump loses its last fluid neighbour (D2Q5) and turns its
+    solute into phi.  Expected values are taken from a run without phase
+    change."""
+    nx, ny, Vm = 5, 6, 0.4
+    mask = np.zeros((1, ny, nx), np.uint8)
+    mask[0, 0:2, :] = 1
+    phi0 = np.where(mask == 1, 1.0, 0.0)
+    phi0[0, 2, 2] = 1.0 - 1e-12  # this fluid cell precipitates in the first step
+    p = dict(dim=2, nx=nx, ny=ny, flow_q=0, solute_q=5, bc=("periodic", "wall", "periodic"), tau_solute=1.0,
+             k_r=0.5, c_eq=0.0, c_init=1.0, molar_volume=Vm)
+    ref = oracle.OracleSim(dict(p, phase_change=0), mask, phi_init=phi0)
+    ref.step(1)
+    _, _, c_ref, phi_ref = ref.fields()
+    s = oracle.OracleSim(dict(p, phase_change=1), mask, phi_init=phi0)
+    s.step(1)
+    assert s.events().tolist() == [[0, 2 + nx * 2, oracle.EV_PRECIPITATE]]
+    cls = s.classes()[0]
+    assert cls[2, 2] == oracle.BOUND and cls[1, 2] == oracle.SOLID
+    assert cls[1, 1] == oracle.BOUND and cls[1, 3] == oracle.BOUND
+    _, _, c, phi = s.fields()
+    excess = phi_ref[0, 2, 2] + Vm * c_ref[0, 2, 2] - 1.0
+    assert excess > 0.0
+    assert phi[0, 2, 2] == 1.0 and c[0, 2, 2] == 0.0
+    assert c[0, 3, 2] == pytest.approx(c_ref[0, 3, 2] + excess / Vm, rel=1e-14)
+    assert c[0, 2, 1] == pytest.approx(c_ref[0, 2, 1], rel=1e-14)
+    assert c[0, 2, 3] == pytest.approx(c_ref[0, 2, 3], rel=1e-14)
+    assert phi[0, 1, 2] == pytest.approx(phi_ref[0, 1, 2] + Vm * c_ref[0, 1, 2], rel=1e-14)

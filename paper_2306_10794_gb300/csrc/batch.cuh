@@ -159,6 +159,13 @@ class BatchEngine final : public IBatch {
         if (nbch_) LB_BCUDA(cudaMemcpy(bch_, bch.data(), sizeof(int2) * nbch_, cudaMemcpyHostToDevice));
         if (nfch_) LB_BCUDA(cudaMemcpy(fch_, fch.data(), sizeof(int2) * nfch_, cudaMemcpyHostToDevice));
         LB_BCUDA(cudaStreamCreateWithFlags(&own_, cudaStreamNonBlocking));
+        {
+            int lo = 0, hi = 0;
+            LB_BCUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+            LB_BCUDA(cudaStreamCreateWithPriority(&aux_, cudaStreamNonBlocking, hi));
+        }
+        LB_BCUDA(cudaEventCreateWithFlags(&fork_, cudaEventDisableTiming));
+        LB_BCUDA(cudaEventCreateWithFlags(&join_, cudaEventDisableTiming));
         // default schedule until autotuned: fluid-list chunks, largest domains
         // first, 8 blocks per SM
         if (set_schedule(3, 1, 8, err)) return 2;
@@ -285,10 +292,22 @@ class BatchEngine final : public IBatch {
         return build_graphs(err);
     }
 
+    // One step of every domain.  The wet-boundary chunks and the fluid-end
+    // gather run on a second stream beside the fluid phase: within each
+    // domain the three touch disjoint population slots, and the gather
+    // depends only on the boundary phase.
     int enqueue(cudaStream_t st, bool odd, std::string& err) {
         const int gf = std::min(grid_, std::max(1, ntiles_));
         const int gb = std::min(grid_, std::max(1, nbch_));
         const int ge = std::min(grid_, std::max(1, nfch_));
+        LB_BCUDA(cudaEventRecord(fork_, st));
+        LB_BCUDA(cudaStreamWaitEvent(aux_, fork_, 0));
+        if (nbch_) {
+            if (odd) kb_bound<T, LG, true><<<gb, LIST_BLOCK, 0, aux_>>>(dd_, bch_, nbch_);
+            else kb_bound<T, LG, false><<<gb, LIST_BLOCK, 0, aux_>>>(dd_, bch_, nbch_);
+        }
+        if (nfch_) kb_fend<T, LG><<<ge, LIST_BLOCK, 0, aux_>>>(dd_, fch_, nfch_);
+        LB_BCUDA(cudaEventRecord(join_, aux_));
         if (policy_ == 3) {
             // list chunks are stored in the tile array as {domain, chunk, 0, 0}
             if (odd) kb_fluid_list4<T, LF, LG, true><<<gf, FLUID_BLOCK, 0, st>>>(dd_, tiles_, ntiles_);
@@ -297,11 +316,7 @@ class BatchEngine final : public IBatch {
             if (odd) kb_fluid<T, LF, LG, true><<<gf, FLUID_BLOCK, 0, st>>>(dd_, tiles_, ntiles_);
             else kb_fluid<T, LF, LG, false><<<gf, FLUID_BLOCK, 0, st>>>(dd_, tiles_, ntiles_);
         }
-        if (nbch_) {
-            if (odd) kb_bound<T, LG, true><<<gb, LIST_BLOCK, 0, st>>>(dd_, bch_, nbch_);
-            else kb_bound<T, LG, false><<<gb, LIST_BLOCK, 0, st>>>(dd_, bch_, nbch_);
-        }
-        if (nfch_) kb_fend<T, LG><<<ge, LIST_BLOCK, 0, st>>>(dd_, fch_, nfch_);
+        LB_BCUDA(cudaStreamWaitEvent(st, join_, 0));
         LB_BCUDA(cudaGetLastError());
         return 0;
     }
@@ -358,6 +373,11 @@ class BatchEngine final : public IBatch {
         doms_.clear();
         if (own_) cudaStreamDestroy(own_);
         own_ = nullptr;
+        if (aux_) cudaStreamDestroy(aux_);
+        aux_ = nullptr;
+        if (fork_) cudaEventDestroy(fork_);
+        if (join_) cudaEventDestroy(join_);
+        fork_ = join_ = nullptr;
     }
 
     std::vector<std::unique_ptr<Engine<T, LF, LG>>> doms_;
@@ -366,7 +386,8 @@ class BatchEngine final : public IBatch {
     int2 *bch_ = nullptr, *fch_ = nullptr;
     int ntiles_ = 0, nbch_ = 0, nfch_ = 0, grid_ = 0, policy_ = 0;
     int lastodd_ = 1;
-    cudaStream_t own_ = nullptr;
+    cudaStream_t own_ = nullptr, aux_ = nullptr;
+    cudaEvent_t fork_ = nullptr, join_ = nullptr;
     cudaGraphExec_t g_even_{}, g_odd_{}, g_pair_{};
     bool graphs_ = false;
 };

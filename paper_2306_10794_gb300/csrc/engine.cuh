@@ -28,6 +28,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "lattice.cuh"
@@ -2149,49 +2150,62 @@ class Engine final : public ISim {
         return (int)std::max<long long>(1, std::min<long long>(b, 152LL * 16));
     }
 
+    // Initial sizes of the wet-boundary list (non-fluid cells with a fluid
+    // solute-lattice neighbour) and of the fluid-end list (fluid cells with a
+    // reactive neighbour at x - e_o), counted on the host to size the lists.
+    // The kinds are copied into a grid with one ghost layer (periodic axes
+    // wrapped, others marked outside) so the count runs with fixed neighbour
+    // offsets, split over host threads by z.
     void count_lists_host(const std::vector<uint8_t>& kind, long long& nb, long long& nf) const {
         const Geo& g = d_.geo;
-        auto inside = [&](int& x, int& y, int& z) {
-            if (x < 0 || x >= g.nx) {
-                if (!g.per_x) return false;
-                x = (x + g.nx) % g.nx;
-            }
-            if (y < 0 || y >= g.ny) {
-                if (!g.per_y) return false;
-                y = (y + g.ny) % g.ny;
-            }
-            if (z < 0 || z >= g.nz) {
-                if (!g.per_z) return false;
-                z = (z + g.nz) % g.nz;
-            }
-            return true;
-        };
-        auto cls = [&](int x, int y, int z) -> int {
-            if (!inside(x, y, z)) return CLS_SOLID;
-            if (kind[g.idx(x, y, z)] == KIND_FLUID) return CLS_FLUID;
-            for (int o = 1; o < LG::Q; ++o) {
-                int xx = x + LG::cx(o), yy = y + LG::cy(o), zz = z + LG::cz(o);
-                if (inside(xx, yy, zz) && kind[g.idx(xx, yy, zz)] == KIND_FLUID) return CLS_BOUND;
-            }
-            return CLS_SOLID;
-        };
-        nb = nf = 0;
-        for (int z = 0; z < g.nz; ++z)
-            for (int y = 0; y < g.ny; ++y)
-                for (int x = 0; x < g.nx; ++x) {
-                    const int c = cls(x, y, z);
-                    if (c == CLS_BOUND) nb++;
-                    if (c == CLS_FLUID) {
-                        for (int o = 1; o < LG::Q; ++o) {
-                            int xx = x - LG::cx(o), yy = y - LG::cy(o), zz = z - LG::cz(o);
-                            if (!inside(xx, yy, zz)) continue;
-                            if (kind[g.idx(xx, yy, zz)] == KIND_REACTIVE) {
-                                nf++;
-                                break;
+        const int X = g.nx + 2, Y = g.ny + 2, Z = g.nz + 2;
+        const uint8_t OUT = 255;
+        std::vector<uint8_t> K((size_t)X * Y * Z, OUT);
+        auto wrap = [](int v, int n, bool per) { return per ? (v + n) % n : v; };
+        for (int z = -1; z <= g.nz; ++z)
+            for (int y = -1; y <= g.ny; ++y)
+                for (int x = -1; x <= g.nx; ++x) {
+                    const int xs = wrap(x, g.nx, g.per_x), ys = wrap(y, g.ny, g.per_y), zs = wrap(z, g.nz, g.per_z);
+                    if (xs < 0 || xs >= g.nx || ys < 0 || ys >= g.ny || zs < 0 || zs >= g.nz) continue;
+                    K[(size_t)(x + 1) + (size_t)X * ((y + 1) + (size_t)Y * (z + 1))] = kind[g.idx(xs, ys, zs)];
+                }
+        long long off[LG::Q];
+        for (int o = 0; o < LG::Q; ++o) off[o] = LG::cx(o) + (long long)X * (LG::cy(o) + (long long)Y * LG::cz(o));
+        const int nt = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        std::vector<long long> cb(nt, 0), cf(nt, 0);
+        std::vector<std::thread> pool;
+        for (int t = 0; t < nt; ++t)
+            pool.emplace_back([&, t]() {
+                long long b = 0, f = 0;
+                for (int z = t; z < g.nz; z += nt)
+                    for (int y = 0; y < g.ny; ++y) {
+                        const uint8_t* row = K.data() + (size_t)X * ((y + 1) + (size_t)Y * (z + 1)) + 1;
+                        for (int x = 0; x < g.nx; ++x) {
+                            const uint8_t* c = row + x;
+                            if (*c == KIND_FLUID) {
+                                for (int o = 1; o < LG::Q; ++o)
+                                    if (c[-off[o]] == KIND_REACTIVE) {
+                                        ++f;
+                                        break;
+                                    }
+                            } else {
+                                for (int o = 1; o < LG::Q; ++o)
+                                    if (c[off[o]] == KIND_FLUID) {
+                                        ++b;
+                                        break;
+                                    }
                             }
                         }
                     }
-                }
+                cb[t] = b;
+                cf[t] = f;
+            });
+        for (auto& th : pool) th.join();
+        nb = nf = 0;
+        for (int t = 0; t < nt; ++t) {
+            nb += cb[t];
+            nf += cf[t];
+        }
     }
 
     // Reclassification and list rebuild (force = 1 at creation: unconditional).

@@ -1,0 +1,988 @@
+// Host side of the device engine (engine.cuh holds the kernels): creation,
+// list sizing, graphs of the step, fields, ledger, events, the adjoint
+// driver and the measurement helper.
+#pragma once
+
+#include <thread>
+#include <vector>
+
+namespace lbrbc {
+
+#define LB_CUDA(call)                                                                     \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            err = std::string(#call) + ": " + cudaGetErrorString(e_);                     \
+            return 2;                                                                     \
+        }                                                                                 \
+    } while (0)
+
+template <typename T, class LF, class LG>
+class Engine final : public ISim {
+   public:
+    ~Engine() override { release(); }
+
+    int init(const lbrbc_params& P, const uint8_t* mask, const lbrbc_init* ini, std::string& err) override {
+        (void)cudaGetLastError();  // do not report an error left by earlier, unrelated calls
+        prm_ = P;
+        Geo& g = d_.geo;
+        g.nx = P.nx;
+        g.ny = P.ny;
+        g.nz = P.dim == 2 ? 1 : P.nz;
+        g.per_x = P.bc[0] == LBRBC_PERIODIC;
+        g.per_y = P.bc[1] == LBRBC_PERIODIC;
+        g.per_z = P.dim == 2 ? 1 : P.bc[2] == LBRBC_PERIODIC;
+        g.open_x = P.bc[0] == LBRBC_OPEN;
+        g.py = g.per_y ? 0 : 1;
+        g.pz = g.per_z ? 0 : 1;
+        g.SX = ((g.nx + 2 + 31) / 32) * 32;
+        g.SY = g.ny + 2 * g.py;
+        g.SZ = g.nz + 2 * g.pz;
+        g.OFF = 32;
+        g.NP = ((g.OFF + (long long)g.SX * g.SY * g.SZ + 64 + 63) / 64) * 64;
+        ncell_ = (long long)g.nx * g.ny * g.nz;
+        if (g.nx >= (1 << 21) || g.ny >= (1 << 21) || g.nz >= (1 << 21)) {
+            err = "grid extent must be below 2^21 cells per axis";
+            return 1;
+        }
+        {
+            const long long qmax = std::max(LF::Q, LG::Q);
+            if (g.NP >= (1LL << 31) || qmax * g.NP >= (1LL << 32)) {
+                err = "grid too large for 32-bit population indices";
+                return 1;
+            }
+        }
+        // physics
+        Phys& p = ph_;
+        const bool trt_f = P.magic_flow >= 0.0, trt_g = P.magic_solute >= 0.0;
+        p.trt_f = trt_f;
+        p.trt_g = trt_g;
+        p.of_sym = 1.0 / P.tau_flow;
+        p.of_anti = trt_f ? 1.0 / (0.5 + P.magic_flow / (P.tau_flow - 0.5)) : p.of_sym;
+        p.og_anti = 1.0 / P.tau_solute;
+        p.og_sym = trt_g ? 1.0 / (0.5 + P.magic_solute / (P.tau_solute - 0.5)) : p.og_anti;
+        if (LG::Q == 9) {
+            p.gcs2 = 1.0 / 3.0;
+            p.gw0 = 4.0 / 9.0;
+            p.gw1 = 1.0 / 9.0;
+        } else {
+            double J0 = P.rest_fraction;
+            if (J0 < 0.0) J0 = (LG::DIM == 2) ? 1.0 / 3.0 : 0.25;
+            p.gcs2 = (1.0 - J0) / LG::DIM;
+            p.gw0 = J0;
+            p.gw1 = p.gcs2 / 2.0;
+            if (P.rest_fraction < 0.0 && LG::DIM == 2) {
+                p.gw0 = 1.0 / 3.0;
+                p.gw1 = 1.0 / 6.0;
+                p.gcs2 = 1.0 / 3.0;
+            }
+        }
+        p.cref = P.c_init != 0.0 ? P.c_init : (P.c_eq != 0.0 ? P.c_eq : P.c_dirichlet);
+        p.c_inlet = P.c_inlet;
+        p.rho_out = P.rho_outlet;
+        p.c_dir = P.c_dirichlet;
+        p.c_eq = P.c_eq;
+        p.k_r = P.k_r;
+        p.gamma = P.tau_solute / (P.tau_solute - 0.5);
+        p.Vm = P.molar_volume;
+        p.rho_init = P.rho_init;
+        p.scheme = P.scheme;
+        p.phase_change = P.phase_change;
+        {
+            PhysT<T>& q = pt_;
+            q.f_sym = T(p.of_sym);
+            q.f_anti = T(p.of_anti);
+            q.g_sym = T(p.og_sym);
+            q.g_anti = T(p.og_anti);
+            for (int i = 0; i < 9; ++i) q.gw[i] = T(0);
+            for (int i = 0; i < LG::Q; ++i) q.gw[i] = T(LG::Q == 9 ? LG::w(i) : (i == 0 ? p.gw0 : p.gw1));
+            q.ics2 = T(1.0 / p.gcs2);
+            q.cref = T(p.cref);
+            q.c_in_d = T(p.c_inlet - p.cref);
+            q.c_dir_d = T(p.c_dir - p.cref);
+            q.c_eq_d = T(p.c_eq - p.cref);
+            q.rho_out = T(p.rho_out);
+            q.k_r = T(p.k_r);
+            q.gamma = T(p.gamma);
+            q.neg_vm = T(-p.Vm);
+        }
+
+        // kinds with ghosts, host side
+        const long long NP = g.NP;
+        std::vector<uint8_t> kind(NP, KIND_OUTSIDE);
+        long long nsolid = 0, nfluid = 0;
+        for (int z = 0; z < g.nz; ++z)
+            for (int y = 0; y < g.ny; ++y)
+                for (int x = 0; x < g.nx; ++x) {
+                    const uint8_t m = mask[x + (long long)g.nx * (y + (long long)g.ny * z)];
+                    kind[g.idx(x, y, z)] = m;
+                    if (m == KIND_FLUID) nfluid++;
+                    else nsolid++;
+                }
+        nfluid_ = nfluid;
+        // list capacities: the initial counts with head room for growth
+        long long nb0 = 0, nf0 = 0;
+        count_lists_host(kind, nb0, nf0);
+        nb0_ = nb0;
+        nf0_ = nf0;
+        auto grow = [&](long long n0) {
+            long long c = std::max<long long>(4 * n0, n0 + ncell_ / 16) + 1024;
+            return (int)std::min<long long>(c, ncell_ + 1024);
+        };
+        d_.cap_b = grow(nb0);
+        d_.cap_f = grow(nf0);
+        d_.cap_e = (int)std::min<long long>(ncell_ + 64, std::max<long long>(1 << 16, ncell_ / 64));
+        // Sweep over the dense grid (default), over a compacted fluid-cell
+        // list (LBRBC_FLUID_SWEEP=list, or a batch schedule) or over staged
+        // row tiles (LBRBC_FLUID_SWEEP=staged).  Measured on GB300 both
+        // alternatives are slower: a warp's 32 list cells span several rows,
+        // so every population load touches more lines; the staged tiles
+        // leave fewer warps to issue an issue-bound cell update.
+        {
+            long long active = 0;
+            for (int z = 0; z < g.nz; ++z)
+                for (int y = 0; y < g.ny; ++y)
+                    for (int x0 = 0; x0 < g.nx; x0 += 32) {
+                        bool any = false;
+                        for (int x = x0; x < std::min(g.nx, x0 + 32) && !any; ++x)
+                            any = mask[x + (long long)g.nx * (y + (long long)g.ny * z)] == KIND_FLUID;
+                        active += any;
+                    }
+            lane_eff_ = active ? (double)nfluid / (32.0 * active) : 1.0;
+            const bool fits = g.nx <= 2048 && g.ny <= 2048 && g.nz <= 1024;
+            const char* env = getenv("LBRBC_FLUID_SWEEP");
+            int want = SWEEP_DENSE;
+            if (env && !strcmp(env, "list")) want = SWEEP_LIST;
+            if (env && !strcmp(env, "dense")) want = SWEEP_DENSE;
+            if (env && !strcmp(env, "staged")) want = SWEEP_STAGED;
+            if (force_list_) want = SWEEP_LIST;
+            // (the list sweep is not combined with phase change)
+            if (want == SWEEP_LIST && !(fits && !P.phase_change)) want = SWEEP_DENSE;
+            sweep_ = want;
+            d_.use_fl = want == SWEEP_LIST;
+            d_.cap_fl = (int)std::min<long long>(ncell_, std::max<long long>(2 * nfluid, nfluid + ncell_ / 8) + 1024);
+        }
+        d_.cap_log = P.event_log_capacity > 0 ? P.event_log_capacity : 0;
+        nchunks_ = (int)((ncell_ + SCAN_CHUNK - 1) / SCAN_CHUNK);
+
+        // device allocations
+        constexpr int QF = LF::Q > 0 ? LF::Q : 0, QG = LG::Q;
+        if (QF) LB_CUDA(dalloc(&d_.F, (size_t)QF * NP));
+        else d_.F = nullptr;
+        LB_CUDA(dalloc(&d_.G, (size_t)QG * NP));
+        LB_CUDA(dalloc(&d_.nw, (size_t)NP));
+        LB_CUDA(dalloc(&d_.kind, (size_t)NP));
+        LB_CUDA(dalloc(&d_.phi, (size_t)NP));
+        LB_CUDA(dalloc(&d_.inlet_ux, (size_t)g.ny * g.nz));
+        LB_CUDA(dalloc(&d_.side, (size_t)4 * g.ny * g.nz));
+        LB_CUDA(dalloc(&d_.nb, 1));
+        LB_CUDA(dalloc(&d_.b_idx, (size_t)d_.cap_b));
+        LB_CUDA(dalloc(&d_.b_word, (size_t)d_.cap_b));
+        LB_CUDA(dalloc(&d_.b_xyz, (size_t)d_.cap_b));
+        LB_CUDA(dalloc(&d_.b_kappa, (size_t)(QG - 1) * d_.cap_b));
+        LB_CUDA(dalloc(&d_.b_fslot, (size_t)(QG - 1) * d_.cap_b));
+        LB_CUDA(dalloc(&d_.bmap, (size_t)NP));
+        LB_CUDA(dalloc(&d_.nf, 1));
+        LB_CUDA(dalloc(&d_.f_idx, (size_t)d_.cap_f));
+        LB_CUDA(dalloc(&d_.f_share, (size_t)(QG - 1) * d_.cap_f));
+        LB_CUDA(dalloc(&d_.nfl, 1));
+        d_.ntiles = 0;
+        d_.tile_on = nullptr;
+        if (sweep_ == SWEEP_STAGED) {
+            const long long nt = (long long)((g.nx + TILE_X - 1) / TILE_X) * g.ny * g.nz;
+            if (nt >= (1LL << 31)) {
+                err = "too many row tiles for the staged sweep";
+                return 1;
+            }
+            d_.ntiles = (int)nt;
+            LB_CUDA(dalloc(&d_.tile_on, (size_t)nt));
+            if (setup_staged(err)) return 2;
+        }
+        if (d_.use_fl) LB_CUDA(dalloc(&d_.fl_xyz, (size_t)d_.cap_fl));
+        else d_.fl_xyz = nullptr;
+        LB_CUDA(cudaMemset(d_.nfl, 0, sizeof(int)));
+        LB_CUDA(dalloc(&d_.nev, 1));
+        LB_CUDA(dalloc(&d_.ev_node, (size_t)d_.cap_e));
+        LB_CUDA(dalloc(&d_.ev_kind, (size_t)d_.cap_e));
+        LB_CUDA(dalloc(&d_.ev_val, (size_t)3 * d_.cap_e));
+        LB_CUDA(dalloc(&d_.ev_w, (size_t)(QG - 1) * d_.cap_e));
+        LB_CUDA(dalloc(&d_.evidx, (size_t)NP));
+        LB_CUDA(dalloc(&d_.nlog, 1));
+        if (d_.cap_log) {
+            LB_CUDA(dalloc(&d_.log_step, (size_t)d_.cap_log));
+            LB_CUDA(dalloc(&d_.log_node, (size_t)d_.cap_log));
+            LB_CUDA(dalloc(&d_.log_kind, (size_t)d_.cap_log));
+        } else {
+            d_.log_step = d_.log_node = nullptr;
+            d_.log_kind = nullptr;
+        }
+        LB_CUDA(dalloc(&d_.step, 1));
+        LB_CUDA(dalloc(&d_.acc, 4));
+        nbacc_ = list_grid(d_.cap_b);
+        LB_CUDA(dalloc(&d_.bacc, (size_t)2 * nbacc_));
+        LB_CUDA(cudaMemset(d_.bacc, 0, 2 * nbacc_ * sizeof(double)));
+        LB_CUDA(dalloc(&d_.err, 1));
+        LB_CUDA(dalloc(&d_.blk, (size_t)nchunks_ + 1));
+        LB_CUDA(cudaStreamCreateWithFlags(&own_, cudaStreamNonBlocking));
+        {
+            // the boundary branch runs beside the fluid sweep; the highest
+            // priority lets its few blocks start first instead of queueing
+            // behind the sweep's
+            int lo = 0, hi = 0;
+            LB_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+            LB_CUDA(cudaStreamCreateWithPriority(&aux_, cudaStreamNonBlocking, hi));
+        }
+        LB_CUDA(cudaEventCreateWithFlags(&fork_, cudaEventDisableTiming));
+        LB_CUDA(cudaEventCreateWithFlags(&join_, cudaEventDisableTiming));
+
+        // uploads
+        std::vector<double> phi(NP, 0.0);
+        std::vector<double> c0((size_t)ncell_);
+        for (int z = 0; z < g.nz; ++z)
+            for (int y = 0; y < g.ny; ++y)
+                for (int x = 0; x < g.nx; ++x) {
+                    const long long t = x + (long long)g.nx * (y + (long long)g.ny * z);
+                    const uint8_t m = mask[t];
+                    phi[g.idx(x, y, z)] = (ini && ini->phi_init) ? ini->phi_init[t] : (m == KIND_REACTIVE ? 1.0 : 0.0);
+                    c0[t] = (ini && ini->c_init) ? ini->c_init[t] : (m == KIND_DIRICHLET ? P.c_dirichlet : P.c_init);
+                }
+        LB_CUDA(cudaMemcpy(d_.kind, kind.data(), NP, cudaMemcpyHostToDevice));
+        LB_CUDA(cudaMemcpy(d_.phi, phi.data(), NP * sizeof(double), cudaMemcpyHostToDevice));
+        if (ini && ini->k_field) {
+            std::vector<double> kf(NP, 0.0);
+            for (int z = 0; z < g.nz; ++z)
+                for (int y = 0; y < g.ny; ++y)
+                    for (int x = 0; x < g.nx; ++x)
+                        kf[g.idx(x, y, z)] = ini->k_field[x + (long long)g.nx * (y + (long long)g.ny * z)];
+            LB_CUDA(dalloc(&d_.kfield, (size_t)NP));
+            LB_CUDA(dalloc(&d_.b_krate, (size_t)d_.cap_b));
+            LB_CUDA(cudaMemcpy(d_.kfield, kf.data(), NP * sizeof(double), cudaMemcpyHostToDevice));
+        } else {
+            d_.kfield = nullptr;
+            d_.b_krate = nullptr;
+        }
+        {
+            std::vector<double> inl((size_t)g.ny * g.nz);
+            for (size_t i = 0; i < inl.size(); ++i) inl[i] = (ini && ini->inlet_ux) ? ini->inlet_ux[i] : P.u_inlet;
+            LB_CUDA(cudaMemcpy(d_.inlet_ux, inl.data(), inl.size() * sizeof(double), cudaMemcpyHostToDevice));
+        }
+        LB_CUDA(cudaMemset(d_.nw, 0, NP * sizeof(uint32_t)));
+        LB_CUDA(cudaMemset(d_.evidx, 0xff, NP * sizeof(int)));
+        LB_CUDA(cudaMemset(d_.bmap, 0xff, NP * sizeof(int)));
+        LB_CUDA(cudaMemset(d_.nev, 0, sizeof(int)));
+        LB_CUDA(cudaMemset(d_.nb, 0, sizeof(int)));
+        LB_CUDA(cudaMemset(d_.nf, 0, sizeof(int)));
+        LB_CUDA(cudaMemset(d_.nlog, 0, sizeof(long long)));
+        LB_CUDA(cudaMemset(d_.step, 0, sizeof(long long)));
+        LB_CUDA(cudaMemset(d_.acc, 0, 4 * sizeof(double)));
+        LB_CUDA(cudaMemset(d_.err, 0, sizeof(int)));
+        LB_CUDA(cudaMemset(d_.side, 0, 4 * sizeof(double) * g.ny * g.nz));
+        if (QF) LB_CUDA(cudaMemset(d_.F, 0, (size_t)QF * NP * sizeof(T)));
+        LB_CUDA(cudaMemset(d_.G, 0, (size_t)QG * NP * sizeof(T)));
+        // ghost cells are solid for every lattice
+        {
+            std::vector<uint32_t> nwh(NP, CLS_SOLID);
+            LB_CUDA(cudaMemcpy(d_.nw, nwh.data(), NP * sizeof(uint32_t), cudaMemcpyHostToDevice));
+        }
+        // classes, lists, initial populations
+        if (rebuild(own_, 0, 1, err)) return 2;
+        double *dc0 = nullptr, *du0 = nullptr;
+        LB_CUDA(talloc(&dc0, (size_t)ncell_));
+        LB_CUDA(cudaMemcpy(dc0, c0.data(), ncell_ * sizeof(double), cudaMemcpyHostToDevice));
+        if (ini && ini->u_init) {
+            LB_CUDA(talloc(&du0, (size_t)3 * ncell_));
+            LB_CUDA(cudaMemcpy(du0, ini->u_init, 3 * ncell_ * sizeof(double), cudaMemcpyHostToDevice));
+        }
+        k_init<T, LF, LG><<<grid_for(ncell_, 256), 256, 0, own_>>>(d_, ph_, dc0, du0);
+        LB_CUDA(cudaGetLastError());
+        LB_CUDA(cudaStreamSynchronize(own_));
+        cudaFree(dc0);
+        if (du0) cudaFree(du0);
+        int hnb = 0, hnf = 0, herr = 0;
+        LB_CUDA(cudaMemcpy(&hnb, d_.nb, sizeof(int), cudaMemcpyDeviceToHost));
+        LB_CUDA(cudaMemcpy(&hnf, d_.nf, sizeof(int), cudaMemcpyDeviceToHost));
+        LB_CUDA(cudaMemcpy(&herr, d_.err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (herr & ERR_OVERFLOW) {
+            err = "internal list capacity exceeded at creation";
+            return 5;
+        }
+        if (hnb != nb0) {
+            err = "device boundary list disagrees with the host count";
+            return 5;
+        }
+        lastodd_ = 1;
+        steps_ = 0;
+        if (build_graphs(err)) return 2;
+        return 0;
+    }
+
+    int step(int64_t n, cudaStream_t s, std::string& err) override {
+        if (batched_) {
+            err = "this domain belongs to a batch: step it with lbrbc_batch_step";
+            return 5;
+        }
+        cudaStream_t st = s ? s : own_;
+        int64_t k = 0;
+        // the state's parity decides which graph comes first
+        while (k < n) {
+            if (!lastodd_ || n - k < 2) {
+                // single step of the pending parity
+                LB_CUDA(cudaGraphLaunch(lastodd_ ? g_even_ : g_odd_, st));
+                lastodd_ ^= 1;
+                k += 1;
+            } else {
+                LB_CUDA(cudaGraphLaunch(g_pair_, st));
+                k += 2;
+            }
+        }
+        steps_ += n;
+        last_stream_ = st;
+        if (!s) LB_CUDA(cudaStreamSynchronize(own_));
+        return 0;
+    }
+
+    int fields(double* u, double* rho, double* c, double* phi, int device, std::string& err) override {
+        LB_CUDA(cudaStreamSynchronize(last_stream_ ? last_stream_ : own_));
+        double *du = u, *dr = rho, *dc = c, *dp = phi;
+        double* tmp = nullptr;
+        if (!device) {
+            int nf = (u ? 3 : 0) + (rho ? 1 : 0) + (c ? 1 : 0) + (phi ? 1 : 0);
+            if (nf == 0) return 0;
+            LB_CUDA(talloc(&tmp, (size_t)nf * ncell_));
+            double* q = tmp;
+            du = u ? q : nullptr;
+            q += u ? 3 * ncell_ : 0;
+            dr = rho ? q : nullptr;
+            q += rho ? ncell_ : 0;
+            dc = c ? q : nullptr;
+            q += c ? ncell_ : 0;
+            dp = phi ? q : nullptr;
+        }
+        k_fields<T, LF, LG><<<grid_for(ncell_, 256), 256, 0, own_>>>(d_, ph_, lastodd_, du, dr, dc, dp);
+        LB_CUDA(cudaGetLastError());
+        LB_CUDA(cudaStreamSynchronize(own_));
+        if (!device) {
+            if (u) LB_CUDA(cudaMemcpy(u, du, 3 * ncell_ * sizeof(double), cudaMemcpyDeviceToHost));
+            if (rho) LB_CUDA(cudaMemcpy(rho, dr, ncell_ * sizeof(double), cudaMemcpyDeviceToHost));
+            if (c) LB_CUDA(cudaMemcpy(c, dc, ncell_ * sizeof(double), cudaMemcpyDeviceToHost));
+            if (phi) LB_CUDA(cudaMemcpy(phi, dp, ncell_ * sizeof(double), cudaMemcpyDeviceToHost));
+            cudaFree(tmp);
+        }
+        return 0;
+    }
+
+    int classes(uint8_t* out, std::string& err) override {
+        LB_CUDA(cudaStreamSynchronize(last_stream_ ? last_stream_ : own_));
+        uint8_t* tmp = nullptr;
+        LB_CUDA(talloc(&tmp, (size_t)ncell_));
+        k_classes<T><<<grid_for(ncell_, 256), 256, 0, own_>>>(d_, tmp);
+        LB_CUDA(cudaGetLastError());
+        LB_CUDA(cudaMemcpyAsync(out, tmp, ncell_, cudaMemcpyDeviceToHost, own_));
+        LB_CUDA(cudaStreamSynchronize(own_));
+        cudaFree(tmp);
+        return 0;
+    }
+
+    int ledger(double* out, std::string& err) override {
+        LB_CUDA(cudaStreamSynchronize(last_stream_ ? last_stream_ : own_));
+        const int nblk = red_blocks();
+        double* part = nullptr;
+        LB_CUDA(talloc(&part, (size_t)2 * nblk + 2));
+        k_reduce_partial<T, LG><<<nblk, RED_BLOCK, 0, own_>>>(d_, ph_, lastodd_, part);
+        k_reduce_final<0><<<1, 32, 0, own_>>>(part, nblk, part + 2 * nblk);
+        LB_CUDA(cudaGetLastError());
+        double sums[2], acc[4];
+        std::vector<double> bacc((size_t)2 * nbacc_);
+        LB_CUDA(cudaMemcpyAsync(sums, part + 2 * nblk, 2 * sizeof(double), cudaMemcpyDeviceToHost, own_));
+        LB_CUDA(cudaMemcpyAsync(acc, d_.acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, own_));
+        LB_CUDA(cudaMemcpyAsync(bacc.data(), d_.bacc, bacc.size() * sizeof(double), cudaMemcpyDeviceToHost, own_));
+        LB_CUDA(cudaStreamSynchronize(own_));
+        for (int b = 0; b < nbacc_; ++b) {
+            acc[0] += bacc[2 * b];
+            acc[1] += bacc[2 * b + 1];
+        }
+        cudaFree(part);
+        out[0] = sums[0];
+        out[1] = prm_.molar_volume > 0.0 ? sums[1] / prm_.molar_volume : 0.0;
+        out[2] = acc[2];
+        out[3] = acc[1];
+        out[4] = acc[0];
+        out[5] = (double)steps_;
+        return 0;
+    }
+
+    // Same reduction on caller-provided scratch (2 * red_blocks() + 2 doubles).
+    int ledger_with_scratch(double* out, double* part, std::string& err) {
+        LB_CUDA(cudaStreamSynchronize(last_stream_ ? last_stream_ : own_));
+        const int nblk = red_blocks();
+        k_reduce_partial<T, LG><<<nblk, RED_BLOCK, 0, own_>>>(d_, ph_, lastodd_, part);
+        k_reduce_final<0><<<1, 32, 0, own_>>>(part, nblk, part + 2 * nblk);
+        LB_CUDA(cudaGetLastError());
+        double sums[2], acc[4];
+        std::vector<double> bacc((size_t)2 * nbacc_);
+        LB_CUDA(cudaMemcpyAsync(sums, part + 2 * nblk, 2 * sizeof(double), cudaMemcpyDeviceToHost, own_));
+        LB_CUDA(cudaMemcpyAsync(acc, d_.acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, own_));
+        LB_CUDA(cudaMemcpyAsync(bacc.data(), d_.bacc, bacc.size() * sizeof(double), cudaMemcpyDeviceToHost, own_));
+        LB_CUDA(cudaStreamSynchronize(own_));
+        for (int b = 0; b < nbacc_; ++b) {
+            acc[0] += bacc[2 * b];
+            acc[1] += bacc[2 * b + 1];
+        }
+        out[0] = sums[0];
+        out[1] = prm_.molar_volume > 0.0 ? sums[1] / prm_.molar_volume : 0.0;
+        out[2] = acc[2];
+        out[3] = acc[1];
+        out[4] = acc[0];
+        out[5] = (double)steps_;
+        return 0;
+    }
+
+    // Mass balance with caller-provided device scratch and no allocation:
+    // one partial pair per block of cells_per_block cells, then the final
+    // sums; scratch holds 2 * max_blocks + 8 doubles.
+    int ledger_scratch(double* out, double* scratch, int max_blocks, long long cells_per_block,
+                       std::string& err) override {
+        const long long nblk = (ncell_ + cells_per_block - 1) / cells_per_block;
+        if (nblk > max_blocks) {
+            err = "grid of " + std::to_string(ncell_) + " cells exceeds the static scratch of this entry point (" +
+                  std::to_string((long long)max_blocks * cells_per_block) + " cells)";
+            return 1;
+        }
+        LB_CUDA(cudaStreamSynchronize(last_stream_ ? last_stream_ : own_));
+        double* tail = scratch + 2 * (size_t)max_blocks;
+        k_reduce_partial<T, LG><<<(int)nblk, RED_BLOCK, 0, own_>>>(d_, ph_, lastodd_, scratch);
+        k_reduce_final<0><<<1, 32, 0, own_>>>(scratch, (int)nblk, tail);
+        k_sum_partials<0><<<1, 32, 0, own_>>>(d_.bacc, nbacc_, d_.acc, tail + 2);
+        LB_CUDA(cudaGetLastError());
+        double h[5];
+        LB_CUDA(cudaMemcpyAsync(h, tail, 5 * sizeof(double), cudaMemcpyDeviceToHost, own_));
+        LB_CUDA(cudaStreamSynchronize(own_));
+        out[0] = h[0];
+        out[1] = prm_.molar_volume > 0.0 ? h[1] / prm_.molar_volume : 0.0;
+        out[2] = h[4];
+        out[3] = h[3];
+        out[4] = h[2];
+        out[5] = (double)steps_;
+        return 0;
+    }
+
+    int events(int64_t* count, int64_t capacity, int64_t* stp, int64_t* node, int32_t* kind, std::string& err) override {
+        LB_CUDA(cudaStreamSynchronize(last_stream_ ? last_stream_ : own_));
+        long long n = 0;
+        LB_CUDA(cudaMemcpy(&n, d_.nlog, sizeof(long long), cudaMemcpyDeviceToHost));
+        n = std::min<long long>(n, d_.cap_log);
+        *count = n;
+        const long long m = std::min<long long>(n, capacity);
+        if (m > 0 && stp) LB_CUDA(cudaMemcpy(stp, d_.log_step, m * sizeof(long long), cudaMemcpyDeviceToHost));
+        if (m > 0 && node) LB_CUDA(cudaMemcpy(node, d_.log_node, m * sizeof(long long), cudaMemcpyDeviceToHost));
+        if (m > 0 && kind) LB_CUDA(cudaMemcpy(kind, d_.log_kind, m * sizeof(int), cudaMemcpyDeviceToHost));
+        return 0;
+    }
+
+    int check(std::string& err) override {
+        LB_CUDA(cudaStreamSynchronize(last_stream_ ? last_stream_ : own_));
+        LB_CUDA(cudaDeviceSynchronize());
+        int herr = 0;
+        LB_CUDA(cudaMemcpy(&herr, d_.err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (herr & ERR_OVERFLOW) {
+            err = "an internal list (events / boundary cells) exceeded its capacity";
+            return 5;
+        }
+        if (herr & ERR_NUMERIC) {
+            err = "non-finite concentration or non-positive density encountered";
+            return 3;
+        }
+        if (herr & ERR_TIMEOUT) {
+            err = "a bounded device wait of the staged sweep gave up";
+            return 4;
+        }
+        return 0;
+    }
+
+    // Accessors used by the batched engine.
+    const PhysT<T>& physt() const { return pt_; }
+    int nbacc() const { return nbacc_; }
+    const Geo& geo() const { return d_.geo; }
+    int host_nb() const { return (int)nb0_; }
+    int host_nf() const { return (int)nf0_; }
+    void set_batched() { batched_ = true; }
+    void force_list(bool v) { force_list_ = v; }
+    bool uses_list() const { return d_.use_fl != 0; }
+    double lane_efficiency() const { return lane_eff_; }
+    int host_nfl() const { return (int)nfluid_; }
+    // Record n steps taken by the batched kernels (parity after them: lastodd).
+    void advance(int64_t n, int lastodd, cudaStream_t st) {
+        steps_ += n;
+        lastodd_ = lastodd;
+        last_stream_ = st;
+    }
+
+    long long fluid_cells() const override { return nfluid_; }
+    long long boundary_cells() const override { return nb0_; }
+    int red_blocks() const { return (int)std::min<long long>(1024, (ncell_ + RED_BLOCK - 1) / RED_BLOCK); }
+    const Dev<T>& dev() const { return d_; }
+    const Phys& phys() const { return ph_; }
+    int last_odd() const { return lastodd_; }
+    cudaStream_t own_stream() const { return own_; }
+    cudaStream_t last_stream() const { return last_stream_; }
+
+    // Gradient of the reacted mass J over the next n steps (the steps are
+    // taken: the simulation ends n steps later, as after lbrbc_step) with
+    // respect to k_r (scalar: sum over cells), c_eq and the per-cell k_r.
+    // sqrt(n) checkpoints of the full state, per-segment recomputation onto
+    // a tape, reverse sweep of the adjoint kernels.
+    int adjoint(int64_t n, double* J, double* dk, double* dceq, double* dk_field, std::string& err) override {
+        if (ph_.phase_change) {
+            err = "the adjoint needs phase change off (events are not differentiable)";
+            return 1;
+        }
+        if (n < 1) {
+            err = "n must be >= 1";
+            return 1;
+        }
+        LB_CUDA(cudaStreamSynchronize(last_stream_ ? last_stream_ : own_));
+        cudaStream_t st = own_;
+        const long long NP = d_.geo.NP;
+        constexpr int QF = LF::Q > 0 ? LF::Q : 0, QG = LG::Q;
+        const int64_t S = std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)n)));
+        const int64_t nseg = (n + S - 1) / S;
+        const size_t fbytes = (size_t)QF * NP * sizeof(T), gbytes = (size_t)QG * NP * sizeof(T);
+        const size_t sbytes = (size_t)4 * d_.geo.ny * d_.geo.nz * sizeof(double);
+        std::vector<void*> tmp;
+        auto get = [&](size_t bytes, void** p) -> cudaError_t {
+            cudaError_t e = cudaMalloc(p, bytes + 16);
+            if (e == cudaSuccess) tmp.push_back(*p);
+            return e;
+        };
+        auto cleanup = [&]() {
+            cudaStreamSynchronize(st);
+            for (void* p : tmp) cudaFree(p);
+        };
+#define LB_ACUDA(call)                                                      \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) {                                            \
+            err = std::string(#call) + ": " + cudaGetErrorString(e_);       \
+            cleanup();                                                      \
+            return 2;                                                       \
+        }                                                                   \
+    } while (0)
+        const int nbk = list_grid(d_.cap_b);
+        void *ck = nullptr, *gtape = nullptr, *utape = nullptr, *lam = nullptr, *nu = nullptr, *dkf = nullptr;
+        void *part = nullptr, *save_phi = nullptr, *save_bacc = nullptr, *save_acc = nullptr, *fin = nullptr;
+        const size_t ckb = fbytes + gbytes + sbytes;
+        LB_ACUDA(get(ckb * (size_t)nseg, &ck));
+        const size_t hbytes = (size_t)(QG - 1) * d_.cap_b * sizeof(T);
+        LB_ACUDA(get(hbytes * (size_t)(S + 1), &gtape));
+        LB_ACUDA(get((size_t)3 * NP * sizeof(float) * (size_t)(S + 1), &utape));
+        LB_ACUDA(get(gbytes, &lam));
+        LB_ACUDA(get(gbytes, &nu));
+        LB_ACUDA(get((size_t)NP * sizeof(double), &dkf));
+        LB_ACUDA(get((size_t)2 * nbk * sizeof(double), &part));
+        LB_ACUDA(get((size_t)NP * sizeof(double), &save_phi));
+        LB_ACUDA(get((size_t)2 * nbacc_ * sizeof(double), &save_bacc));
+        LB_ACUDA(get(4 * sizeof(double), &save_acc));
+        LB_ACUDA(get(ckb, &fin));
+        auto save_state = [&](char* dst) -> cudaError_t {
+            cudaError_t e = cudaSuccess;
+            if (QF) e = cudaMemcpyAsync(dst, d_.F, fbytes, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dst + fbytes, d_.G, gbytes, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dst + fbytes + gbytes, d_.side, sbytes, cudaMemcpyDeviceToDevice, st);
+            return e;
+        };
+        auto load_state = [&](const char* src) -> cudaError_t {
+            cudaError_t e = cudaSuccess;
+            if (QF) e = cudaMemcpyAsync(d_.F, src, fbytes, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(d_.G, src + fbytes, gbytes, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(d_.side, src + fbytes + gbytes, sbytes, cudaMemcpyDeviceToDevice, st);
+            return e;
+        };
+        double led0[6];
+        if (int rc = ledger(led0, err)) {
+            cleanup();
+            return rc;
+        }
+        // forward pass with checkpoints
+        std::vector<int> ck_odd(nseg);
+        for (int64_t sgi = 0; sgi < nseg; ++sgi) {
+            LB_ACUDA(save_state((char*)ck + ckb * sgi));
+            ck_odd[sgi] = lastodd_;
+            const int64_t len = std::min<int64_t>(S, n - sgi * S);
+            if (int rc = step(len, st, err)) {
+                cleanup();
+                return rc;
+            }
+        }
+        double led1[6];
+        if (int rc = ledger(led1, err)) {
+            cleanup();
+            return rc;
+        }
+        const int fin_odd = lastodd_;
+        const int64_t fin_steps = steps_;
+        LB_ACUDA(save_state((char*)fin));
+        LB_ACUDA(cudaMemcpyAsync(save_phi, d_.phi, NP * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        LB_ACUDA(cudaMemcpyAsync(save_bacc, d_.bacc, 2 * nbacc_ * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        LB_ACUDA(cudaMemcpyAsync(save_acc, d_.acc, 4 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        // reverse sweep
+        LB_ACUDA(cudaMemsetAsync(lam, 0, gbytes, st));
+        LB_ACUDA(cudaMemsetAsync(dkf, 0, NP * sizeof(double), st));
+        LB_ACUDA(cudaMemsetAsync(part, 0, 2 * nbk * sizeof(double), st));
+        const dim3 g3((d_.geo.nx + FLUID_BLOCK - 1) / FLUID_BLOCK, d_.geo.ny, d_.geo.nz);
+        for (int64_t sgi = nseg - 1; sgi >= 0; --sgi) {
+            LB_ACUDA(load_state((const char*)ck + ckb * sgi));
+            lastodd_ = ck_odd[sgi];
+            const int64_t len = std::min<int64_t>(S, n - sgi * S);
+            T* ht = (T*)gtape;
+            float* ut = (float*)utape;
+            const size_t hstride = (size_t)(QG - 1) * d_.cap_b;
+            // recompute the segment; the step kernels write the tape as they go
+            for (int64_t j = 1; j <= len; ++j) {
+                Dev<T> dv = d_;
+                dv.tape_u = QF ? ut + (size_t)j * 3 * NP : nullptr;
+                dv.tape_h = ht + (size_t)j * hstride;
+                if (enqueue_step(st, !lastodd_, err, nullptr, &dv)) {
+                    cleanup();
+                    return 2;
+                }
+                lastodd_ ^= 1;
+            }
+            for (int64_t j = len; j >= 1; --j) {
+                k_adj_fluid<T, LG><<<g3, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_, (const T*)lam, (T*)nu,
+                                                               QF ? ut + (size_t)j * 3 * NP : nullptr);
+                k_adj_bound<T, LG><<<nbk, LIST_BLOCK, 0, st>>>(d_, ph_, pt_, (const T*)lam, (T*)nu,
+                                                               ht + (size_t)j * hstride, (double*)dkf, (double*)part);
+                k_adj_stream<T, LG><<<g3, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_, (const T*)nu, (T*)lam);
+            }
+            LB_ACUDA(cudaGetLastError());
+        }
+        // the recomputation re-accumulated phi and the ledger: restore the
+        // state reached by the forward pass
+        LB_ACUDA(load_state((const char*)fin));
+        LB_ACUDA(cudaMemcpyAsync(d_.phi, save_phi, NP * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        LB_ACUDA(cudaMemcpyAsync(d_.bacc, save_bacc, 2 * nbacc_ * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        LB_ACUDA(cudaMemcpyAsync(d_.acc, save_acc, 4 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        lastodd_ = fin_odd;
+        steps_ = fin_steps;
+        std::vector<double> hp((size_t)2 * nbk);
+        LB_ACUDA(cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        std::vector<double> hk;
+        if (dk_field) {
+            hk.resize(NP);
+            LB_ACUDA(cudaMemcpyAsync(hk.data(), dkf, NP * sizeof(double), cudaMemcpyDeviceToHost, st));
+        }
+        LB_ACUDA(cudaStreamSynchronize(st));
+        double sk = 0.0, sc = 0.0;
+        for (int b = 0; b < nbk; ++b) {
+            sk += hp[2 * b];
+            sc += hp[2 * b + 1];
+        }
+        if (J) *J = led1[4] - led0[4];
+        if (dk) *dk = sk;
+        if (dceq) *dceq = sc;
+        if (dk_field) {
+            const Geo& g = d_.geo;
+            for (int z = 0; z < g.nz; ++z)
+                for (int y = 0; y < g.ny; ++y)
+                    for (int x = 0; x < g.nx; ++x)
+                        dk_field[x + (long long)g.nx * (y + (long long)g.ny * z)] = hk[g.idx(x, y, z)];
+        }
+#undef LB_ACUDA
+        cleanup();
+        return 0;
+    }
+
+   private:
+    // Allocation owned by the simulation until release().
+    template <typename U>
+    cudaError_t dalloc(U** p, size_t n) {
+        cudaError_t e = cudaMalloc((void**)p, n * sizeof(U) + 16);
+        if (e == cudaSuccess) allocs_.push_back((void*)*p);
+        return e;
+    }
+    // Temporary allocation, freed by the caller.
+    template <typename U>
+    static cudaError_t talloc(U** p, size_t n) {
+        return cudaMalloc((void**)p, n * sizeof(U) + 16);
+    }
+
+    static int grid_for(long long n, int block) {
+        long long b = (n + block - 1) / block;
+        return (int)std::max<long long>(1, std::min<long long>(b, 152LL * 16));
+    }
+
+    // Initial sizes of the wet-boundary list (non-fluid cells with a fluid
+    // solute-lattice neighbour) and of the fluid-end list (fluid cells with a
+    // reactive neighbour at x - e_o), counted on the host to size the lists.
+    // The kinds are copied into a grid with one ghost layer (periodic axes
+    // wrapped, others marked outside) so the count runs with fixed neighbour
+    // offsets, split over host threads by z.
+    void count_lists_host(const std::vector<uint8_t>& kind, long long& nb, long long& nf) const {
+        const Geo& g = d_.geo;
+        const int X = g.nx + 2, Y = g.ny + 2, Z = g.nz + 2;
+        const uint8_t OUT = 255;
+        std::vector<uint8_t> K((size_t)X * Y * Z, OUT);
+        auto wrap = [](int v, int n, bool per) { return per ? (v + n) % n : v; };
+        for (int z = -1; z <= g.nz; ++z)
+            for (int y = -1; y <= g.ny; ++y)
+                for (int x = -1; x <= g.nx; ++x) {
+                    const int xs = wrap(x, g.nx, g.per_x), ys = wrap(y, g.ny, g.per_y), zs = wrap(z, g.nz, g.per_z);
+                    if (xs < 0 || xs >= g.nx || ys < 0 || ys >= g.ny || zs < 0 || zs >= g.nz) continue;
+                    K[(size_t)(x + 1) + (size_t)X * ((y + 1) + (size_t)Y * (z + 1))] = kind[g.idx(xs, ys, zs)];
+                }
+        long long off[LG::Q];
+        for (int o = 0; o < LG::Q; ++o) off[o] = LG::cx(o) + (long long)X * (LG::cy(o) + (long long)Y * LG::cz(o));
+        const int nt = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        std::vector<long long> cb(nt, 0), cf(nt, 0);
+        std::vector<std::thread> pool;
+        for (int t = 0; t < nt; ++t)
+            pool.emplace_back([&, t]() {
+                long long b = 0, f = 0;
+                for (int z = t; z < g.nz; z += nt)
+                    for (int y = 0; y < g.ny; ++y) {
+                        const uint8_t* row = K.data() + (size_t)X * ((y + 1) + (size_t)Y * (z + 1)) + 1;
+                        for (int x = 0; x < g.nx; ++x) {
+                            const uint8_t* c = row + x;
+                            if (*c == KIND_FLUID) {
+                                for (int o = 1; o < LG::Q; ++o)
+                                    if (c[-off[o]] == KIND_REACTIVE) {
+                                        ++f;
+                                        break;
+                                    }
+                            } else {
+                                for (int o = 1; o < LG::Q; ++o)
+                                    if (c[off[o]] == KIND_FLUID) {
+                                        ++b;
+                                        break;
+                                    }
+                            }
+                        }
+                    }
+                cb[t] = b;
+                cf[t] = f;
+            });
+        for (auto& th : pool) th.join();
+        nb = nf = 0;
+        for (int t = 0; t < nt; ++t) {
+            nb += cb[t];
+            nf += cf[t];
+        }
+    }
+
+    // Reclassification and list rebuild (force = 1 at creation: unconditional).
+    int rebuild(cudaStream_t st, int lastodd, int force, std::string& err) {
+        k_reclassify<T, LF, LG><<<grid_for(ncell_, 256), 256, 0, st>>>(d_, ph_, lastodd, force);
+        if (sweep_ == SWEEP_STAGED) k_tile_flags<T><<<grid_for((long long)d_.ntiles * 32, 256), 256, 0, st>>>(d_, force);
+        for (int which = 0; which < (d_.use_fl ? 3 : 2); ++which) {
+            k_count<T, LG><<<nchunks_, 256, 0, st>>>(d_, which, force);
+            k_scan<T><<<1, 1024, 0, st>>>(d_, nchunks_, which, force);
+            k_write_lists<T, LG><<<nchunks_, 256, 0, st>>>(d_, ph_, which, force);
+        }
+        LB_CUDA(cudaGetLastError());
+        return 0;
+    }
+
+    // One time step; with `ev` (5 events) the kernel groups are bracketed by
+    // event records: fluid sweep, boundary list, fluid ends, phase change.
+    int enqueue_step(cudaStream_t st, bool odd, std::string& err, cudaEvent_t* ev = nullptr,
+                     const Dev<T>* dv = nullptr) {
+        const Dev<T>& d_ = dv ? *dv : this->d_;
+        const Geo& g = d_.geo;
+        dim3 grid((g.nx + FLUID_BLOCK - 1) / FLUID_BLOCK, g.ny, g.nz);
+        if (ev) LB_CUDA(cudaEventRecord(ev[0], st));
+        // Without per-group timing the boundary list and the fluid ends run
+        // on a second stream beside the fluid sweep: the three kernels touch
+        // disjoint population slots (each slot is read and written by one
+        // cell per step), and the fluid ends depend only on the boundary list.
+        const bool fork = ev == nullptr;
+        if (fork) {
+            LB_CUDA(cudaEventRecord(fork_, st));
+            LB_CUDA(cudaStreamWaitEvent(aux_, fork_, 0));
+            const int lg = list_grid(d_.cap_b);
+            if (odd) k_bound<T, LG, true><<<lg, LIST_BLOCK, 0, aux_>>>(d_, ph_, pt_);
+            else k_bound<T, LG, false><<<lg, LIST_BLOCK, 0, aux_>>>(d_, ph_, pt_);
+            k_fend<T, LG><<<list_grid(d_.cap_f), LIST_BLOCK, 0, aux_>>>(d_, ph_);
+            LB_CUDA(cudaEventRecord(join_, aux_));
+        }
+        if (sweep_ == SWEEP_STAGED) {
+            const size_t sm = (size_t)staged_stages<T>() * staged_stage_bytes<T, LF, LG>();
+            if (odd) k_fluid_staged<T, LF, LG, true><<<sgrid_, TILE_X, sm, st>>>(d_, ph_, pt_);
+            else k_fluid_staged<T, LF, LG, false><<<sgrid_, TILE_X, sm, st>>>(d_, ph_, pt_);
+        } else if (d_.use_fl) {
+            const int gl = (int)((d_.cap_fl + FLUID_BLOCK - 1) / FLUID_BLOCK);
+            if (odd) k_fluid_list<T, LF, LG, true><<<gl, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_);
+            else k_fluid_list<T, LF, LG, false><<<gl, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_);
+        } else {
+            if (odd) k_fluid<T, LF, LG, true><<<grid, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_);
+            else k_fluid<T, LF, LG, false><<<grid, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_);
+        }
+        if (fork) {
+            LB_CUDA(cudaStreamWaitEvent(st, join_, 0));
+        } else {
+            LB_CUDA(cudaEventRecord(ev[1], st));
+            const int lg = list_grid(d_.cap_b);
+            if (odd) k_bound<T, LG, true><<<lg, LIST_BLOCK, 0, st>>>(d_, ph_, pt_);
+            else k_bound<T, LG, false><<<lg, LIST_BLOCK, 0, st>>>(d_, ph_, pt_);
+            LB_CUDA(cudaEventRecord(ev[2], st));
+            k_fend<T, LG><<<list_grid(d_.cap_f), LIST_BLOCK, 0, st>>>(d_, ph_);
+            LB_CUDA(cudaEventRecord(ev[3], st));
+        }
+        if (ph_.phase_change) {
+            const int eg = 152 * 2;
+            const int lo = odd ? 1 : 0;
+            k_ev_mark<T><<<eg, 256, 0, st>>>(d_);
+            k_ev_compute<T, LF, LG><<<eg, 256, 0, st>>>(d_, ph_, lo);
+            k_ev_apply_self<T, LF, LG><<<eg, 256, 0, st>>>(d_, ph_, lo);
+            k_ev_neighbours<T, LG><<<eg, 256, 0, st>>>(d_, ph_, lo);
+            if (rebuild(st, lo, 0, err)) return 2;
+            k_ev_reset<T><<<eg, 256, 0, st>>>(d_);
+            k_step_end<T><<<1, 1, 0, st>>>(d_);
+        }
+        if (ev) LB_CUDA(cudaEventRecord(ev[4], st));
+        LB_CUDA(cudaGetLastError());
+        return 0;
+    }
+
+   public:
+    // Number of kernel launches of one step.
+    int launches_per_step() const override { return 3 + (ph_.phase_change ? 5 + 3 * 2 + 2 + 1 : 0); }
+
+    // Run n steps without graphs, timing each kernel group with CUDA events on
+    // the stream the kernels run on; ms[g] = mean duration of group g.
+    int profile(int64_t n, cudaStream_t s, double* ms, std::string& err) override {
+        cudaStream_t st = s ? s : own_;
+        n = std::max<int64_t>(1, std::min<int64_t>(n, 4096));
+        std::vector<cudaEvent_t> ev((size_t)5 * n);
+        for (auto& e : ev) LB_CUDA(cudaEventCreate(&e));
+        for (int64_t k = 0; k < n; ++k) {
+            const bool odd = !lastodd_;
+            if (enqueue_step(st, odd, err, &ev[(size_t)5 * k])) return 2;
+            lastodd_ ^= 1;
+        }
+        steps_ += n;
+        last_stream_ = st;
+        LB_CUDA(cudaStreamSynchronize(st));
+        double acc[4] = {0, 0, 0, 0};
+        for (int64_t k = 0; k < n; ++k)
+            for (int q = 0; q < 4; ++q) {
+                float t = 0.f;
+                LB_CUDA(cudaEventElapsedTime(&t, ev[(size_t)5 * k + q], ev[(size_t)5 * k + q + 1]));
+                acc[q] += t;
+            }
+        for (int q = 0; q < 4; ++q) ms[q] = acc[q] / (double)n;
+        for (auto& e : ev) cudaEventDestroy(e);
+        return 0;
+    }
+
+   private:
+    // Shared memory and persistent grid of the staged sweep: as many CTAs as
+    // fit on the device at once (never more than there are tiles).
+    int setup_staged(std::string& err) {
+        const size_t sm = (size_t)staged_stages<T>() * staged_stage_bytes<T, LF, LG>();
+        int occ = 64;
+        int dev = 0, nsm = 0;
+        LB_CUDA(cudaGetDevice(&dev));
+        LB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        auto occ_of = [&](auto kern) -> int {
+            int o = 0;
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return -1;
+            // the persistent grid assumes every CTA of the occupancy
+            // estimate is resident: ask for the largest shared-memory carveout
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+                return -1;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, TILE_X, sm) != cudaSuccess) return -1;
+            return o;
+        };
+        const int o[2] = {occ_of(k_fluid_staged<T, LF, LG, false>), occ_of(k_fluid_staged<T, LF, LG, true>)};
+        for (int k = 0; k < 2; ++k) {
+            if (o[k] < 0) {
+                err = std::string("staged sweep setup: ") + cudaGetErrorString(cudaGetLastError());
+                return 2;
+            }
+            occ = std::min(occ, o[k]);
+        }
+        occ = std::max(1, occ);
+        sgrid_ = (int)std::max<long long>(1, std::min<long long>((long long)nsm * occ, d_.ntiles));
+        return 0;
+    }
+
+    static int list_grid(int cap) {
+        return (int)std::max(1, std::min(152 * 8, (cap + LIST_BLOCK - 1) / LIST_BLOCK));
+    }
+
+    int build_graphs(std::string& err) {
+        cudaStream_t cs;
+        LB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        auto cap = [&](cudaGraphExec_t* out, int mode) -> int {
+            cudaGraph_t gr;
+            LB_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            int r = 0;
+            if (mode == 0) r = enqueue_step(cs, false, err);
+            else if (mode == 1) r = enqueue_step(cs, true, err);
+            else {
+                r = enqueue_step(cs, false, err);
+                if (!r) r = enqueue_step(cs, true, err);
+            }
+            cudaError_t e = cudaStreamEndCapture(cs, &gr);
+            if (r) return r;
+            if (e != cudaSuccess) {
+                err = std::string("graph capture: ") + cudaGetErrorString(e);
+                return 2;
+            }
+            LB_CUDA(cudaGraphInstantiate(out, gr, 0));
+            cudaGraphDestroy(gr);
+            return 0;
+        };
+        if (cap(&g_even_, 0) || cap(&g_odd_, 1) || cap(&g_pair_, 2)) {
+            cudaStreamDestroy(cs);
+            return 2;
+        }
+        graphs_ = true;
+        cudaStreamDestroy(cs);
+        return 0;
+    }
+
+    void release() {
+        if (graphs_) {
+            cudaGraphExecDestroy(g_even_);
+            cudaGraphExecDestroy(g_odd_);
+            cudaGraphExecDestroy(g_pair_);
+            graphs_ = false;
+        }
+        if (own_) cudaStreamSynchronize(own_);
+        for (void* p : allocs_) cudaFree(p);
+        allocs_.clear();
+        if (own_) cudaStreamDestroy(own_);
+        own_ = nullptr;
+        if (aux_) cudaStreamDestroy(aux_);
+        aux_ = nullptr;
+        if (fork_) cudaEventDestroy(fork_);
+        if (join_) cudaEventDestroy(join_);
+        fork_ = join_ = nullptr;
+    }
+
+    lbrbc_params prm_{};
+    Dev<T> d_{};
+    Phys ph_{};
+    PhysT<T> pt_{};
+    long long ncell_ = 0, nfluid_ = 0, nb0_ = 0, nf0_ = 0;
+    int nchunks_ = 0;
+    int nbacc_ = 0;
+    int lastodd_ = 1;
+    int64_t steps_ = 0;
+    cudaStream_t own_ = nullptr, last_stream_ = nullptr, aux_ = nullptr;
+    cudaEvent_t fork_ = nullptr, join_ = nullptr;
+    int sweep_ = SWEEP_DENSE;
+    int sgrid_ = 1;
+    cudaGraphExec_t g_even_{}, g_odd_{}, g_pair_{};
+    bool graphs_ = false;
+    bool batched_ = false;
+    bool force_list_ = false;
+    double lane_eff_ = 1.0;
+    std::vector<void*> allocs_;
+};
+
+#undef LB_CUDA
+
+}  // namespace lbrbc

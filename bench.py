@@ -124,6 +124,29 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
+# GB300 FP64 rate (nominal, no measured figure exists for it): 1.25 TFLOP/s,
+# i.e. 625 G FP64 pipe operations/s (a DFMA is 2 FLOP; DADD and DMUL take a
+# pipe slot each as well).
+FP64_PEAK_GOPS = 625.0
+
+
+def fp64_ops_per_cell(kernel_src_hash, wkey):
+    """FP64 pipe operations (DFMA + DADD + DMUL) per fluid cell of one
+    k_fluid launch from the committed ncu count, if it was taken on the
+    current kernel source and this workload (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_fluid_channel_fp64.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None, None
+    m = re.search(r"source_sha256:\s*([0-9a-f]+)", txt)
+    t = re.search(r"fp64_ops_per_fluid_cell:\s*([0-9.eE+]+)", txt)
+    w = re.search(r"workload_key:\s*(\S+)", txt)
+    if not m or not t or not w or m.group(1) != kernel_src_hash or w.group(1) != wkey:
+        return None, None
+    return float(t.group(1)), os.path.relpath(path, ROOT)
+
+
 def workload_key(a):
     """Identifies the workload an ncu summary was taken on."""
     return "%s-%s-%s-theta%g-pe%g-da%g-%s" % (a.case, a.size, a.precision, a.theta, a.pe, a.da, a.sweep)
@@ -493,6 +516,23 @@ def main():
     khash = kernel_hash()
     traffic, traffic_src = ncu_traffic(khash, workload_key(a))
     step_gbs = bytes_launch / (ms_max / K * 1e-3) / 1e9
+    kname = "%s (fluid-cell stream-collide, D3Q19 + D3Q7)" % (
+        "k_fluid_staged" if a.sweep == "staged" else "k_fluid_list" if a.sweep == "list" else "k_fluid")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": kname, "bytes_per_launch": bytes_launch, "ms_per_launch": kms[0],
+                "peak_kind": peak_kind, "traffic_source": traffic_src, "kernel_source_sha256": khash,
+                "step_algorithmic_gbs": step_gbs}
+    if a.precision == "fp64":
+        # the FP64 sweep is bound by GB300's FP64 rate, not by HBM
+        opc, osrc = fp64_ops_per_cell(khash, workload_key(a))
+        if opc is not None:
+            gops = opc * fluid / (kms[0] * 1e-3) / 1e9
+            roofline = {"bound": "alu", "achieved": gops, "peak": FP64_PEAK_GOPS, "unit": "G FP64 ops/s",
+                        "frac": gops / FP64_PEAK_GOPS, "traffic": None, "kernel": kname,
+                        "ops_per_fluid_cell": opc, "ops_source": osrc, "ms_per_launch": kms[0],
+                        "peak_kind": "nominal FP64 rate 1.25 TFLOP/s = 625 G pipe ops/s (none measured)",
+                        "kernel_source_sha256": khash,
+                        "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak}}
 
     # accuracy of this precision against the FP64 path (outside the timed region)
     acc = None
@@ -549,14 +589,7 @@ def main():
                        "fluid_sweep": a.sweep,
                        "l2_policy": "no flush: populations %.2f GB resident > L2 %.0f MB" % (
                            (26 * (4 if a.precision == "fp32" else 8) * mask.size) / 1e9, L2_BYTES / 1e6)},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "%s (fluid-cell stream-collide, D3Q19 + D3Q7)" % (
-                             "k_fluid_staged" if a.sweep == "staged" else "k_fluid_list" if a.sweep == "list"
-                             else "k_fluid"),
-                         "bytes_per_launch": bytes_launch, "ms_per_launch": kms[0], "peak_kind": peak_kind,
-                         "traffic_source": traffic_src, "kernel_source_sha256": khash,
-                         "step_algorithmic_gbs": step_gbs},
+            "roofline": roofline,
             "kernel_ms_per_step": {"fluid": kms[0], "boundary": kms[1], "fluid_ends": kms[2],
                                    "phase_change": kms[3]},
             "gpu_launches": int(launches * K),

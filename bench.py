@@ -45,7 +45,7 @@ def args_():
     ap.add_argument("--pack-n", type=int, default=512, help="edge of the sphere-pack case")
     ap.add_argument("--case", choices=["channel", "spherepack", "batch", "adjoint", "molins"], default="channel",
                     help="channel: the headline workload; spherepack: 512^3 precipitation with phase change")
-    ap.add_argument("--sweep", choices=["dense", "staged", "list"], default="dense",
+    ap.add_argument("--sweep", choices=["dense", "list"], default="dense",
                     help="fluid-cell sweep of the library (LBRBC_FLUID_SWEEP)")
     ap.add_argument("--molins-cases", type=str, default="4", help="Table 2 cases of --case molins, e.g. 1,2,3,4")
     ap.add_argument("--scale", type=float, default=1.0, help="resolution of --case molins (1 = the paper's 600x1200)")
@@ -171,7 +171,7 @@ def ncu_traffic(kernel_src_hash, wkey):
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("engine.cuh", "lattice.cuh", "pairs.cuh", "staged.cuh"):
+    for f in ("engine.cuh", "lattice.cuh", "pairs.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2306_10794_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -517,7 +517,7 @@ def main():
     traffic, traffic_src = ncu_traffic(khash, workload_key(a))
     step_gbs = bytes_launch / (ms_max / K * 1e-3) / 1e9
     kname = "%s (fluid-cell stream-collide, D3Q19 + D3Q7)" % (
-        "k_fluid_staged" if a.sweep == "staged" else "k_fluid_list" if a.sweep == "list" else "k_fluid")
+        "k_fluid_list" if a.sweep == "list" else "k_fluid")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": kname, "bytes_per_launch": bytes_launch, "ms_per_launch": kms[0],
                 "peak_kind": peak_kind, "traffic_source": traffic_src, "kernel_source_sha256": khash,

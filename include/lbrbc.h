@@ -29,12 +29,9 @@
  *   - There is no CPU fallback: a machine without a usable GPU gets
  *     LBRBC_ERR_CUDA from lbrbc_create.
  *   - The fluid-cell sweep is chosen at creation by the environment variable
- *     LBRBC_FLUID_SWEEP: "dense" (default; one thread per grid cell),
- *     "staged" (persistent blocks stage row tiles in shared memory with bulk
- *     asynchronous copies) or "list" (compacted fluid cells; not with
- *     phase change, where it falls back to "dense").  All give the same
- *     results up to the order of floating-point operations, which is the
- *     same in all three.
+ *     LBRBC_FLUID_SWEEP: "dense" (default; one thread per grid cell) or
+ *     "list" (compacted fluid cells; not with phase change, where it falls
+ *     back to "dense").  Both give bitwise identical results.
  */
 #ifndef LBRBC_H
 #define LBRBC_H
@@ -53,7 +50,7 @@ typedef enum {
     LBRBC_ERR_ARG = 1,         /* invalid parameter or size                        */
     LBRBC_ERR_CUDA = 2,        /* CUDA runtime error (message has the CUDA text)    */
     LBRBC_ERR_NUMERIC = 3,     /* non-finite or non-positive density/concentration  */
-    LBRBC_ERR_TIMEOUT = 4,     /* a bounded device wait gave up (lbrbc_check)        */
+    LBRBC_ERR_TIMEOUT = 4,     /* reserved for bounded device waits                 */
     LBRBC_ERR_STATE = 5,       /* capacity of an internal list exceeded             */
     LBRBC_ERR_UNSUPPORTED = 6  /* lattice / option combination not built            */
 } lbrbc_status;

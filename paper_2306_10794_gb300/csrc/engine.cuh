@@ -39,8 +39,8 @@ enum : uint32_t { CLS_FLUID = 0, CLS_BOUND = 1, CLS_SOLID = 2 };
 enum : uint8_t { KIND_FLUID = 0, KIND_REACTIVE = 1, KIND_DIRICHLET = 2, KIND_OUTSIDE = 3 };
 enum : int { EV_DISSOLVE = 1, EV_PRECIPITATE = 2 };
 enum : int { ERR_NUMERIC = 1, ERR_OVERFLOW = 2, ERR_TIMEOUT = 4 };
-// fluid sweep: dense grid, compacted fluid list, or staged row tiles
-enum : int { SWEEP_DENSE = 0, SWEEP_LIST = 1, SWEEP_STAGED = 2 };
+// fluid sweep: dense grid or compacted fluid list
+enum : int { SWEEP_DENSE = 0, SWEEP_LIST = 1 };
 
 // node word of a fluid cell: bits 0-1 class, bits FBIT.. "flow source
 // x - e_i is not fluid" for i = 1..QF-1, bits GBIT.. "solute source
@@ -178,9 +178,6 @@ struct Dev {
     int cap_fl;
     int* nfl;
     uint32_t* fl_xyz;
-    // staged sweep: one flag per row tile (1 = the tile has a fluid cell)
-    int ntiles;
-    uint8_t* tile_on;
     // adjoint recomputation tape (null in ordinary steps): fluid velocity
     // per cell (3 floats) and the streamed h_obar of each reactive link
     float* tape_u;
@@ -351,9 +348,8 @@ __device__ __forceinline__ void st_pop(T* p, T v) {
 #endif
 }
 
-// Where a fluid cell's pre-collision populations come from.  GlobalSrc reads
-// the AA slot (read_slot) directly; the staged sweep reads the plain slots
-// from shared memory and only the swapped slots of inactive sources from HBM.
+// Where a fluid cell's pre-collision populations come from: GlobalSrc reads
+// the AA slot (read_slot) directly from HBM.
 template <typename T, class LF, class LG, bool ODD>
 struct GlobalSrc {
     const T* __restrict__ F;
@@ -370,7 +366,7 @@ struct GlobalSrc {
 };
 
 // One fluid cell (x, y, z) of one step with node word w; shared by the
-// single-domain, staged and batched sweeps.
+// single-domain and batched sweeps.
 template <typename T, class LF, class LG, bool ODD, class Src>
 __device__ __forceinline__ void fluid_cell_src(const Dev<T>& a, const Phys& p, const PhysT<T>& q, int x, int y, int z,
                                                uint32_t id, uint32_t w, const Nbr32& d, const Src& src) {
@@ -1439,6 +1435,5 @@ __global__ void k_sum_partials(const double* bacc, int nblocks, const double* ac
 }
 
 }  // namespace lbrbc
-#include "staged.cuh"
 #include "adjoint.cuh"
 #include "engine_host.cuh"

@@ -133,11 +133,9 @@ class Engine final : public ISim {
         d_.cap_f = grow(nf0);
         d_.cap_e = (int)std::min<long long>(ncell_ + 64, std::max<long long>(1 << 16, ncell_ / 64));
         // Sweep over the dense grid (default), over a compacted fluid-cell
-        // list (LBRBC_FLUID_SWEEP=list, or a batch schedule) or over staged
-        // row tiles (LBRBC_FLUID_SWEEP=staged).  Measured on GB300 both
-        // alternatives are slower: a warp's 32 list cells span several rows,
-        // so every population load touches more lines; the staged tiles
-        // leave fewer warps to issue an issue-bound cell update.
+        // list (LBRBC_FLUID_SWEEP=list, or a batch schedule).  Measured on
+        // GB300 the list is slower: a warp's 32 list cells span several rows,
+        // so every population load touches more lines.
         {
             long long active = 0;
             for (int z = 0; z < g.nz; ++z)
@@ -154,7 +152,6 @@ class Engine final : public ISim {
             int want = SWEEP_DENSE;
             if (env && !strcmp(env, "list")) want = SWEEP_LIST;
             if (env && !strcmp(env, "dense")) want = SWEEP_DENSE;
-            if (env && !strcmp(env, "staged")) want = SWEEP_STAGED;
             if (force_list_) want = SWEEP_LIST;
             // (the list sweep is not combined with phase change)
             if (want == SWEEP_LIST && !(fits && !P.phase_change)) want = SWEEP_DENSE;
@@ -186,18 +183,6 @@ class Engine final : public ISim {
         LB_CUDA(dalloc(&d_.f_idx, (size_t)d_.cap_f));
         LB_CUDA(dalloc(&d_.f_share, (size_t)(QG - 1) * d_.cap_f));
         LB_CUDA(dalloc(&d_.nfl, 1));
-        d_.ntiles = 0;
-        d_.tile_on = nullptr;
-        if (sweep_ == SWEEP_STAGED) {
-            const long long nt = (long long)((g.nx + TILE_X - 1) / TILE_X) * g.ny * g.nz;
-            if (nt >= (1LL << 31)) {
-                err = "too many row tiles for the staged sweep";
-                return 1;
-            }
-            d_.ntiles = (int)nt;
-            LB_CUDA(dalloc(&d_.tile_on, (size_t)nt));
-            if (setup_staged(err)) return 2;
-        }
         if (d_.use_fl) LB_CUDA(dalloc(&d_.fl_xyz, (size_t)d_.cap_fl));
         else d_.fl_xyz = nullptr;
         LB_CUDA(cudaMemset(d_.nfl, 0, sizeof(int)));
@@ -492,10 +477,6 @@ class Engine final : public ISim {
             err = "non-finite concentration or non-positive density encountered";
             return 3;
         }
-        if (herr & ERR_TIMEOUT) {
-            err = "a bounded device wait of the staged sweep gave up";
-            return 4;
-        }
         return 0;
     }
 
@@ -772,7 +753,6 @@ class Engine final : public ISim {
     // Reclassification and list rebuild (force = 1 at creation: unconditional).
     int rebuild(cudaStream_t st, int lastodd, int force, std::string& err) {
         k_reclassify<T, LF, LG><<<grid_for(ncell_, 256), 256, 0, st>>>(d_, ph_, lastodd, force);
-        if (sweep_ == SWEEP_STAGED) k_tile_flags<T><<<grid_for((long long)d_.ntiles * 32, 256), 256, 0, st>>>(d_, force);
         for (int which = 0; which < (d_.use_fl ? 3 : 2); ++which) {
             k_count<T, LG><<<nchunks_, 256, 0, st>>>(d_, which, force);
             k_scan<T><<<1, 1024, 0, st>>>(d_, nchunks_, which, force);
@@ -804,11 +784,7 @@ class Engine final : public ISim {
             k_fend<T, LG><<<list_grid(d_.cap_f), LIST_BLOCK, 0, aux_>>>(d_, ph_);
             LB_CUDA(cudaEventRecord(join_, aux_));
         }
-        if (sweep_ == SWEEP_STAGED) {
-            const size_t sm = (size_t)staged_stages<T>() * staged_stage_bytes<T, LF, LG>();
-            if (odd) k_fluid_staged<T, LF, LG, true><<<sgrid_, TILE_X, sm, st>>>(d_, ph_, pt_);
-            else k_fluid_staged<T, LF, LG, false><<<sgrid_, TILE_X, sm, st>>>(d_, ph_, pt_);
-        } else if (d_.use_fl) {
+        if (d_.use_fl) {
             const int gl = (int)((d_.cap_fl + FLUID_BLOCK - 1) / FLUID_BLOCK);
             if (odd) k_fluid_list<T, LF, LG, true><<<gl, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_);
             else k_fluid_list<T, LF, LG, false><<<gl, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_);
@@ -875,38 +851,6 @@ class Engine final : public ISim {
     }
 
    private:
-    // Shared memory and persistent grid of the staged sweep: as many CTAs as
-    // fit on the device at once (never more than there are tiles).
-    int setup_staged(std::string& err) {
-        const size_t sm = (size_t)staged_stages<T>() * staged_stage_bytes<T, LF, LG>();
-        int occ = 64;
-        int dev = 0, nsm = 0;
-        LB_CUDA(cudaGetDevice(&dev));
-        LB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        auto occ_of = [&](auto kern) -> int {
-            int o = 0;
-            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return -1;
-            // the persistent grid assumes every CTA of the occupancy
-            // estimate is resident: ask for the largest shared-memory carveout
-            if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
-                return -1;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, TILE_X, sm) != cudaSuccess) return -1;
-            return o;
-        };
-        const int o[2] = {occ_of(k_fluid_staged<T, LF, LG, false>), occ_of(k_fluid_staged<T, LF, LG, true>)};
-        for (int k = 0; k < 2; ++k) {
-            if (o[k] < 0) {
-                err = std::string("staged sweep setup: ") + cudaGetErrorString(cudaGetLastError());
-                return 2;
-            }
-            occ = std::min(occ, o[k]);
-        }
-        occ = std::max(1, occ);
-        sgrid_ = (int)std::max<long long>(1, std::min<long long>((long long)nsm * occ, d_.ntiles));
-        return 0;
-    }
-
     static int list_grid(int cap) {
         return (int)std::max(1, std::min(152 * 8, (cap + LIST_BLOCK - 1) / LIST_BLOCK));
     }
@@ -974,7 +918,6 @@ class Engine final : public ISim {
     cudaStream_t own_ = nullptr, last_stream_ = nullptr, aux_ = nullptr;
     cudaEvent_t fork_ = nullptr, join_ = nullptr;
     int sweep_ = SWEEP_DENSE;
-    int sgrid_ = 1;
     cudaGraphExec_t g_even_{}, g_odd_{}, g_pair_{};
     bool graphs_ = false;
     bool batched_ = false;

@@ -114,31 +114,29 @@ def test_sphere_pack_512_cropped(precision):
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_sweeps_bitwise_identical_channel(precision, monkeypatch):
-    # the staged, dense and list sweeps run the same per-cell arithmetic in
+    # the dense and list sweeps run the same per-cell arithmetic in
     # the same order: identical fields after steps of both parities, at the
     # benchmark's size and through the graphs it times
     p, mask, extra = workloads.case_channel(nx=256, ny=128, nz=128, theta_deg=30.0, Pe=10.0, Da=1.0)
     p["precision"] = precision
     out = {}
-    for mode in ("staged", "dense", "list"):
+    for mode in ("dense", "list"):
         monkeypatch.setenv("LBRBC_FLUID_SWEEP", mode)
         s = lbrbc.Sim(p, mask, **extra)
         s.step(7)
         out[mode] = (s.fields(), s.ledger())
         s.close()
-    for mode in ("dense", "list"):
-        for a, b in zip(out["staged"][0], out[mode][0]):
-            assert np.array_equal(a, b), mode
-        assert out["staged"][1] == out[mode][1], mode
+    for a, b in zip(out["dense"][0], out["list"][0]):
+        assert np.array_equal(a, b)
+    assert out["dense"][1] == out["list"][1]
 
 
-@pytest.mark.parametrize("mode", ["staged", "dense"])
-def test_concurrent_boundary_branch_matches_sequential(mode, monkeypatch):
+def test_concurrent_boundary_branch_matches_sequential(monkeypatch):
     # the step graphs run the boundary list and the fluid ends on a second
     # stream beside the fluid sweep; the timed profile path runs the three
     # kernels one after the other.  Disjoint slots: identical results, also
     # with phase change.
-    monkeypatch.setenv("LBRBC_FLUID_SWEEP", mode)
+    monkeypatch.setenv("LBRBC_FLUID_SWEEP", "dense")
     p, mask, extra = workloads.case_sphere_pack(n=96, molar_volume=0.05)
     p = dict(p)
     p["precision"] = "fp64"

@@ -19,10 +19,9 @@ pytestmark = pytest.mark.gpu
 TOL64 = 1e-11
 
 
-@pytest.fixture(params=["dense", "list", "staged"])
+@pytest.fixture(params=["dense", "list"])
 def sweep(request, monkeypatch):
-    # the fluid sweep runs over the dense grid, the compacted fluid list or
-    # staged row tiles
+    # the fluid sweep runs over the dense grid or the compacted fluid list
     monkeypatch.setenv("LBRBC_FLUID_SWEEP", request.param)
     return request.param
 
@@ -137,13 +136,10 @@ def test_fp32_relative_l2(sweep):
 
 
 @pytest.mark.parametrize("c_init,phi_solid,kind", [(3.0, 1.0, 2), (0.0, 0.03, 1)])
-@pytest.mark.parametrize("mode", ["dense", "staged"])
-def test_phase_change_events_identical_fp64(c_init, phi_solid, kind, mode, monkeypatch):
+def test_phase_change_events_identical_fp64(c_init, phi_solid, kind):
     # Events are threshold decisions on FP64 values that differ from the
     # oracle's by rounding only; identity holds unless a cell lands within
-    # rounding of a threshold.  The tile flags of the staged sweep follow
-    # the reclassified cells.
-    monkeypatch.setenv("LBRBC_FLUID_SWEEP", mode)
+    # rounding of a threshold.
     shape = (14, 16, 36)
     mask = pack(shape, 7)
     rng = np.random.default_rng(8)

@@ -316,19 +316,37 @@ __device__ __forceinline__ uint32_t off32(const Nbr32& d, int i) {
                       (L::cz(i) > 0 ? d.zp : (L::cz(i) < 0 ? d.zm : 0)));
 }
 
+// Population layout: cells in blocks of 32 consecutive padded indices (a
+// row segment: rows start at multiples of 32), the Q populations of a block
+// stored one after the other, 32 values each.  Slot of population i of cell
+// id: (id - id % 32) Q + 32 i + id % 32.  A warp's 32 cells read and write
+// one 128-byte line per population, and the Q lines of a block are
+// contiguous, so a warp streams Q * 128 bytes from one region instead of
+// one line from each of Q arrays.
+template <class L>
+__host__ __device__ __forceinline__ uint32_t pslot(int i, uint32_t id) {
+    return (id & ~31u) * (uint32_t)L::Q + (uint32_t)i * 32u + (id & 31u);
+}
+template <class L>
+__host__ __device__ __forceinline__ long long pslot64(int i, long long id) {
+    return (id & ~31LL) * (long long)L::Q + (long long)i * 32 + (id & 31LL);
+}
+
 // Slot read by a cell for direction i: its own slot i (even step) or the
 // slot opp(i) of the source x - e_i (odd step); an inactive source swaps
 // the two (the value there is the cell's own f*_opp(i)).
 template <class L, bool ODD>
 __device__ __forceinline__ uint32_t read_slot(uint32_t id, const Nbr32& d, uint32_t NP, int i, bool inactive) {
-    const uint32_t own = (uint32_t)i * NP + id;
-    const uint32_t nbr = (uint32_t)L::opp(i) * NP + id + off32<L>(d, L::opp(i));
+    (void)NP;
+    const uint32_t own = pslot<L>(i, id);
+    const uint32_t nbr = pslot<L>(L::opp(i), id + off32<L>(d, L::opp(i)));
     return (ODD == inactive) ? own : nbr;
 }
 
 template <class L, bool ODD>
 __device__ __forceinline__ uint32_t write_slot(uint32_t id, const Nbr32& d, uint32_t NP, int i) {
-    return ODD ? (uint32_t)i * NP + id + off32<L>(d, i) : (uint32_t)L::opp(i) * NP + id;
+    (void)NP;
+    return ODD ? pslot<L>(i, id + off32<L>(d, i)) : pslot<L>(L::opp(i), id);
 }
 
 template <typename T>
@@ -759,7 +777,8 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_fend(const Dev<T> a, const Phys 
 // ---------------------------------------------------------------------------
 template <class L, typename T>
 __device__ __forceinline__ long long post_slot(long long id, const Nbr& d, int i, long long NP, bool lastodd) {
-    return lastodd ? (long long)i * NP + id + off<L>(d, i) : (long long)L::opp(i) * NP + id;
+    (void)NP;
+    return lastodd ? pslot64<L>(i, id + off<L>(d, i)) : pslot64<L>(L::opp(i), id);
 }
 
 template <class L, typename T>
@@ -1278,7 +1297,7 @@ __global__ void k_init(const Dev<T> a, const Phys p, const double* __restrict__ 
                 for (int i = 0; i < LF::Q; ++i) {
                     const double eu = LF::cx(i) * ux + LF::cy(i) * uy + LF::cz(i) * uz;
                     const double feq = LF::w(i) * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
-                    a.F[(long long)i * NP + id + off<LF>(d, i)] = T(feq - LF::w(i));
+                    a.F[pslot64<LF>(i, id + off<LF>(d, i))] = T(feq - LF::w(i));
                 }
             }
         }
@@ -1288,7 +1307,7 @@ __global__ void k_init(const Dev<T> a, const Phys p, const double* __restrict__ 
             for (int i = 0; i < LG::Q; ++i) {
                 const double eu = LG::cx(i) * ux + LG::cy(i) * uy + LG::cz(i) * uz;
                 const double w = gweight<LG>(p, i);
-                a.G[(long long)i * NP + id + off<LG>(d, i)] = T(C * w * (1.0 + eu * ics2) - w * p.cref);
+                a.G[pslot64<LG>(i, id + off<LG>(d, i))] = T(C * w * (1.0 + eu * ics2) - w * p.cref);
             }
         }
         if (g.open_x && x == g.nx - 1) {

@@ -332,21 +332,55 @@ __host__ __device__ __forceinline__ long long pslot64(int i, long long id) {
     return (id & ~31LL) * (long long)L::Q + (long long)i * 32 + (id & 31LL);
 }
 
+// Slots of a cell and of its neighbours in the blocked layout.  Rows start
+// at multiples of 32 and y / z neighbour offsets are multiples of the row
+// length, so a y / z shift moves whole blocks: the slot of population j at
+// id + e is the slot of j at the x-shifted cell plus the y / z offset times
+// Q.  Per cell: the population-0 slots of the cell and of its x neighbours
+// (periodic wrap included) and the y / z offsets scaled by Q.
+template <class L>
+struct Blk {
+    uint32_t b0, bxp, bxm;
+    uint32_t yp, ym, zp, zm;
+};
+
+template <class L>
+__device__ __forceinline__ Blk<L> blk_of(uint32_t id, const Nbr32& d) {
+    Blk<L> k;
+    k.b0 = pslot<L>(0, id);
+    k.bxp = pslot<L>(0, id + (uint32_t)d.xp);
+    k.bxm = pslot<L>(0, id + (uint32_t)d.xm);
+    k.yp = (uint32_t)d.yp * (uint32_t)L::Q;
+    k.ym = (uint32_t)d.ym * (uint32_t)L::Q;
+    k.zp = (uint32_t)d.zp * (uint32_t)L::Q;
+    k.zm = (uint32_t)d.zm * (uint32_t)L::Q;
+    return k;
+}
+
+// slot of population j at the neighbour id + e_n
+template <class L>
+__device__ __forceinline__ uint32_t nslot(const Blk<L>& k, int j, int n) {
+    uint32_t s = (L::cx(n) > 0 ? k.bxp : (L::cx(n) < 0 ? k.bxm : k.b0)) + (uint32_t)j * 32u;
+    if (L::cy(n) > 0) s += k.yp;
+    else if (L::cy(n) < 0) s += k.ym;
+    if (L::cz(n) > 0) s += k.zp;
+    else if (L::cz(n) < 0) s += k.zm;
+    return s;
+}
+
 // Slot read by a cell for direction i: its own slot i (even step) or the
 // slot opp(i) of the source x - e_i (odd step); an inactive source swaps
 // the two (the value there is the cell's own f*_opp(i)).
 template <class L, bool ODD>
-__device__ __forceinline__ uint32_t read_slot(uint32_t id, const Nbr32& d, uint32_t NP, int i, bool inactive) {
-    (void)NP;
-    const uint32_t own = pslot<L>(i, id);
-    const uint32_t nbr = pslot<L>(L::opp(i), id + off32<L>(d, L::opp(i)));
+__device__ __forceinline__ uint32_t read_slot(const Blk<L>& k, int i, bool inactive) {
+    const uint32_t own = k.b0 + (uint32_t)i * 32u;
+    const uint32_t nbr = nslot<L>(k, L::opp(i), L::opp(i));
     return (ODD == inactive) ? own : nbr;
 }
 
 template <class L, bool ODD>
-__device__ __forceinline__ uint32_t write_slot(uint32_t id, const Nbr32& d, uint32_t NP, int i) {
-    (void)NP;
-    return ODD ? pslot<L>(i, id + off32<L>(d, i)) : pslot<L>(L::opp(i), id);
+__device__ __forceinline__ uint32_t write_slot(const Blk<L>& k, int i) {
+    return ODD ? nslot<L>(k, i, i) : k.b0 + (uint32_t)L::opp(i) * 32u;
 }
 
 template <typename T>
@@ -372,15 +406,11 @@ template <typename T, class LF, class LG, bool ODD>
 struct GlobalSrc {
     const T* __restrict__ F;
     const T* __restrict__ G;
-    uint32_t id, NP;
-    Nbr32 d;
+    Blk<LF> kF;
+    Blk<LG> kG;
     __device__ __forceinline__ bool general() const { return false; }
-    __device__ __forceinline__ T f(int i, bool inactive) const {
-        return ld_pop(F + read_slot<LF, ODD>(id, d, NP, i, inactive));
-    }
-    __device__ __forceinline__ T g(int i, bool inactive) const {
-        return ld_pop(G + read_slot<LG, ODD>(id, d, NP, i, inactive));
-    }
+    __device__ __forceinline__ T f(int i, bool inactive) const { return ld_pop(F + read_slot<LF, ODD>(kF, i, inactive)); }
+    __device__ __forceinline__ T g(int i, bool inactive) const { return ld_pop(G + read_slot<LG, ODD>(kG, i, inactive)); }
 };
 
 // One fluid cell (x, y, z) of one step with node word w; shared by the
@@ -390,7 +420,6 @@ __device__ __forceinline__ void fluid_cell_src(const Dev<T>& a, const Phys& p, c
                                                uint32_t id, uint32_t w, const Nbr32& d, const Src& src) {
     constexpr int QF = LF::Q, QG = LG::Q;
     const Geo& g = a.geo;
-    const uint32_t NP = (uint32_t)g.NP;
     T* __restrict__ F = a.F;
     T* __restrict__ G = a.G;
     const bool inlet = g.open_x && x == 0;
@@ -458,7 +487,7 @@ __device__ __forceinline__ void fluid_cell_src(const Dev<T>& a, const Phys& p, c
     if constexpr (QF > 0) {
         flow_pairs<LF, T>(reinterpret_cast<T(&)[QF]>(f), rho, ux, uy, uz, p, q);
 #pragma unroll
-        for (int i = 0; i < QF; ++i) st_pop(F + write_slot<LF, ODD>(id, d, NP, i), f[i]);
+        for (int i = 0; i < QF; ++i) st_pop(F + write_slot<LF, ODD>(src.kF, i), f[i]);
     }
     T C;
     solute_pairs<LG, T>(gg, C, ux, uy, uz, p, q);
@@ -469,7 +498,7 @@ __device__ __forceinline__ void fluid_cell_src(const Dev<T>& a, const Phys& p, c
         a.tape_u[3 * (size_t)id + 2] = (float)uz;
     }
 #pragma unroll
-    for (int i = 0; i < QG; ++i) st_pop(G + write_slot<LG, ODD>(id, d, NP, i), gg[i]);
+    for (int i = 0; i < QG; ++i) st_pop(G + write_slot<LG, ODD>(src.kG, i), gg[i]);
     if (outlet) {
         const int face = y + g.ny * z;
         a.side[4 * face + 0] = (double)ux;
@@ -486,7 +515,7 @@ __device__ __forceinline__ void fluid_cell(const Dev<T>& a, const Phys& p, const
     const uint32_t w = a.nw[id];
     if ((w & 3u) != CLS_FLUID) return;
     const Nbr32 d = nbr32(g, x, y, z);
-    const GlobalSrc<T, LF, LG, ODD> src{a.F, a.G, id, (uint32_t)g.NP, d};
+    const GlobalSrc<T, LF, LG, ODD> src{a.F, a.G, blk_of<LF>(id, d), blk_of<LG>(id, d)};
     fluid_cell_src<T, LF, LG, ODD>(a, p, q, x, y, z, id, w, d, src);
 }
 
@@ -631,7 +660,6 @@ __device__ __forceinline__ void bound_entry(const Dev<T>& a, const Phys& p, cons
                                             DiffSum<T>& dacc) {
     constexpr int Q = LG::Q;
     const Geo& g = a.geo;
-    const uint32_t NP = (uint32_t)g.NP;
     T* __restrict__ G = a.G;
     const T cref = q.cref;
     const T gam = q.gamma, ics2 = q.ics2;
@@ -639,12 +667,13 @@ __device__ __forceinline__ void bound_entry(const Dev<T>& a, const Phys& p, cons
     unpack_xyz(a.b_xyz[e], x, y, z);
     const uint32_t b = (uint32_t)g.idx(x, y, z);
     const Nbr32 d = nbr32(g, x, y, z);
+    const Blk<LG> kb = blk_of<LG>(b, d);
     const uint32_t bw = a.b_word[e];
     T gp[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const bool inactive = i > 0 && ((bw >> (i - 1)) & 1u);
-        gp[i] = G[read_slot<LG, ODD>(b, d, NP, i, inactive)];
+        gp[i] = G[read_slot<LG, ODD>(kb, i, inactive)];
     }
     T gq[Q];
 #pragma unroll
@@ -696,7 +725,7 @@ __device__ __forceinline__ void bound_entry(const Dev<T>& a, const Phys& p, cons
     if (!isfinite(C)) *a.err |= ERR_NUMERIC;
     collide_solute<LG, T>(gq, C, T(0), T(0), T(0), p, q);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) G[write_slot<LG, ODD>(b, d, NP, i)] = gq[i];
+    for (int i = 0; i < Q; ++i) G[write_slot<LG, ODD>(kb, i)] = gq[i];
     const int sg = ms.sign();
     if (dir) {
         dacc.merge(ms);
@@ -1273,7 +1302,6 @@ __global__ void k_step_end(const Dev<T> a) {
 template <typename T, class LF, class LG>
 __global__ void k_init(const Dev<T> a, const Phys p, const double* __restrict__ c0, const double* __restrict__ u0) {
     const Geo& g = a.geo;
-    const long long NP = g.NP;
     const long long total = (long long)g.nx * g.ny * g.nz;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {

@@ -748,7 +748,7 @@ __device__ __forceinline__ void bound_entry(const Dev<T>& a, const Phys& p, cons
 }
 
 template <typename T, class LG, bool ODD>
-__global__ void __launch_bounds__(LIST_BLOCK) k_bound(const Dev<T> a, const Phys p, const PhysT<T> q) {
+__global__ void __launch_bounds__(LIST_BLOCK, 4) k_bound(const Dev<T> a, const Phys p, const PhysT<T> q) {
     const int n = *a.nb;
     DiffSum<T> racc, dacc;  // reacted mass and Dirichlet inflow of this thread
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)

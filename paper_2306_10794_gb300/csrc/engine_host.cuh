@@ -204,6 +204,13 @@ class Engine final : public ISim {
         LB_CUDA(dalloc(&d_.step, 1));
         LB_CUDA(dalloc(&d_.acc, 4));
         nbacc_ = list_grid(d_.cap_b);
+        // Grids of the boundary-list and fluid-end kernels: sized to the
+        // lists at creation with 25 % head room (a grid-stride loop covers
+        // any growth).  A grid sized to the capacity would hold most of the
+        // GPU's thread slots with idle threads while the fluid sweep runs.
+        bgrid_ = (int)std::min<long long>(nbacc_, std::max<long long>(1, (nb0_ * 5 / 4 + LIST_BLOCK - 1) / LIST_BLOCK));
+        fgrid_ = (int)std::min<long long>(list_grid(d_.cap_f),
+                                          std::max<long long>(1, (nf0_ * 5 / 4 + LIST_BLOCK - 1) / LIST_BLOCK));
         LB_CUDA(dalloc(&d_.bacc, (size_t)2 * nbacc_));
         LB_CUDA(cudaMemset(d_.bacc, 0, 2 * nbacc_ * sizeof(double)));
         LB_CUDA(dalloc(&d_.err, 1));
@@ -778,10 +785,9 @@ class Engine final : public ISim {
         if (fork) {
             LB_CUDA(cudaEventRecord(fork_, st));
             LB_CUDA(cudaStreamWaitEvent(aux_, fork_, 0));
-            const int lg = list_grid(d_.cap_b);
-            if (odd) k_bound<T, LG, true><<<lg, LIST_BLOCK, 0, aux_>>>(d_, ph_, pt_);
-            else k_bound<T, LG, false><<<lg, LIST_BLOCK, 0, aux_>>>(d_, ph_, pt_);
-            k_fend<T, LG><<<list_grid(d_.cap_f), LIST_BLOCK, 0, aux_>>>(d_, ph_);
+            if (odd) k_bound<T, LG, true><<<bgrid_, LIST_BLOCK, 0, aux_>>>(d_, ph_, pt_);
+            else k_bound<T, LG, false><<<bgrid_, LIST_BLOCK, 0, aux_>>>(d_, ph_, pt_);
+            k_fend<T, LG><<<fgrid_, LIST_BLOCK, 0, aux_>>>(d_, ph_);
             LB_CUDA(cudaEventRecord(join_, aux_));
         }
         if (d_.use_fl) {
@@ -796,11 +802,10 @@ class Engine final : public ISim {
             LB_CUDA(cudaStreamWaitEvent(st, join_, 0));
         } else {
             LB_CUDA(cudaEventRecord(ev[1], st));
-            const int lg = list_grid(d_.cap_b);
-            if (odd) k_bound<T, LG, true><<<lg, LIST_BLOCK, 0, st>>>(d_, ph_, pt_);
-            else k_bound<T, LG, false><<<lg, LIST_BLOCK, 0, st>>>(d_, ph_, pt_);
+            if (odd) k_bound<T, LG, true><<<bgrid_, LIST_BLOCK, 0, st>>>(d_, ph_, pt_);
+            else k_bound<T, LG, false><<<bgrid_, LIST_BLOCK, 0, st>>>(d_, ph_, pt_);
             LB_CUDA(cudaEventRecord(ev[2], st));
-            k_fend<T, LG><<<list_grid(d_.cap_f), LIST_BLOCK, 0, st>>>(d_, ph_);
+            k_fend<T, LG><<<fgrid_, LIST_BLOCK, 0, st>>>(d_, ph_);
             LB_CUDA(cudaEventRecord(ev[3], st));
         }
         if (ph_.phase_change) {
@@ -912,7 +917,7 @@ class Engine final : public ISim {
     PhysT<T> pt_{};
     long long ncell_ = 0, nfluid_ = 0, nb0_ = 0, nf0_ = 0;
     int nchunks_ = 0;
-    int nbacc_ = 0;
+    int nbacc_ = 0, bgrid_ = 1, fgrid_ = 1;
     int lastodd_ = 1;
     int64_t steps_ = 0;
     cudaStream_t own_ = nullptr, last_stream_ = nullptr, aux_ = nullptr;

@@ -38,7 +38,7 @@ namespace lbrbc {
 enum : uint32_t { CLS_FLUID = 0, CLS_BOUND = 1, CLS_SOLID = 2 };
 enum : uint8_t { KIND_FLUID = 0, KIND_REACTIVE = 1, KIND_DIRICHLET = 2, KIND_OUTSIDE = 3 };
 enum : int { EV_DISSOLVE = 1, EV_PRECIPITATE = 2 };
-enum : int { ERR_NUMERIC = 1, ERR_OVERFLOW = 2, ERR_TIMEOUT = 4 };
+enum : int { ERR_NUMERIC = 1, ERR_OVERFLOW = 2 };
 // fluid sweep: dense grid or compacted fluid list
 enum : int { SWEEP_DENSE = 0, SWEEP_LIST = 1 };
 
@@ -408,7 +408,6 @@ struct GlobalSrc {
     const T* __restrict__ G;
     Blk<LF> kF;
     Blk<LG> kG;
-    __device__ __forceinline__ bool general() const { return false; }
     __device__ __forceinline__ T f(int i, bool inactive) const { return ld_pop(F + read_slot<LF, ODD>(kF, i, inactive)); }
     __device__ __forceinline__ T g(int i, bool inactive) const { return ld_pop(G + read_slot<LG, ODD>(kG, i, inactive)); }
 };
@@ -424,7 +423,7 @@ __device__ __forceinline__ void fluid_cell_src(const Dev<T>& a, const Phys& p, c
     T* __restrict__ G = a.G;
     const bool inlet = g.open_x && x == 0;
     const bool outlet = g.open_x && x == g.nx - 1;
-    const bool plain = (w >> FBIT) == 0u && !inlet && !outlet && !src.general();
+    const bool plain = (w >> FBIT) == 0u && !inlet && !outlet;
 
     // Warps whose cells all read the plain slots take a path with no
     // per-direction tests; the others pick, per direction, the plain slot or

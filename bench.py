@@ -170,9 +170,14 @@ def ncu_traffic(kernel_src_hash, wkey):
 
 
 def kernel_hash():
+    """Hash of the fluid kernel's device sources with comments and blank
+    space removed (a comment edit does not change the kernel)."""
     h = hashlib.sha256()
     for f in ("engine.cuh", "lattice.cuh", "pairs.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2306_10794_gb300", "csrc", f), "rb").read())
+        txt = open(os.path.join(ROOT, "paper_2306_10794_gb300", "csrc", f)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        txt = re.sub(r"//[^\n]*", "", txt)
+        h.update("\n".join(line.strip() for line in txt.splitlines() if line.strip()).encode())
     return h.hexdigest()[:16]
 
 

@@ -3,8 +3,10 @@
 // type T (float: deviation storage, double) and the flow / solute lattices.
 //
 // Storage ("AA pattern", one population array per lattice, in place):
-//   every population slot A[i][cell] of a padded dense grid (SoA, x fastest,
-//   rows padded to 32 cells, ghost layers on non-periodic axes).  After an
+//   population slot A[i][cell] for every cell of a padded dense grid (x
+//   fastest, rows padded to 32 cells, ghost layers on non-periodic axes),
+//   the cells grouped in blocks of 32 whose Q populations are stored one
+//   after the other (pslot).  After an
 //   even step the post-collision value f*_i(x) sits in A[opp(i)][x]; after
 //   an odd step in A[i][x + e_i], whatever lies at x + e_i (fluid, solid or
 //   ghost).  Writes never depend on the geometry; the boundary rules are

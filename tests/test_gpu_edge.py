@@ -1,0 +1,93 @@
+"""Degenerate inputs through the C ABI against the FP64 oracle: no wet
+boundary cells at all (an all-fluid periodic box: empty lists, zero
+ledger), no fluid cells at all, periodic axes one cell wide (a cell is its
+own neighbour), a single fluid cell enclosed by reactive solid (every link
+reactive), and a pure solute lattice next to the coupled one."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2306_10794_gb300 import lbrbc
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-11
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2306_10794_gb300 import _build
+
+    _build.build()
+    oracle.build()
+
+
+def both(p, mask, steps, **init):
+    g = lbrbc.Sim(p, mask, **init)
+    o = oracle.OracleSim(p, mask, **init)
+    g.step(steps)
+    o.step(steps)
+    g.check()
+    assert np.array_equal(g.classes(), o.classes())
+    for a, b in zip(g.fields(), o.fields()):
+        assert np.abs(a - b).max() < TOL
+    return g, o
+
+
+BASE = dict(dim=3, flow_q=19, solute_q=7, tau_flow=0.8, magic_flow=3.0 / 16.0, tau_solute=0.9, k_r=0.1, c_eq=0.5,
+            c_init=1.0, molar_volume=0.2, precision="fp64")
+
+
+def test_all_fluid_box_has_empty_lists_and_zero_ledger():
+    shape = (6, 7, 33)
+    rng = np.random.default_rng(1)
+    u0 = 0.02 * rng.standard_normal(shape + (3,))
+    c0 = 1.0 + 0.1 * rng.standard_normal(shape)
+    p = dict(BASE, nx=33, ny=7, nz=6, bc=("periodic",) * 3)
+    g, o = both(p, np.zeros(shape, np.uint8), 21, u_init=u0, c_init=c0)
+    assert g.info()["boundary_cells"] == 0
+    L = g.ledger()
+    assert L["reacted"] == 0.0 and L["dirichlet_in"] == 0.0
+    assert abs(L["solute"] - c0.sum()) < 1e-10 * c0.sum()
+
+
+def test_no_fluid_cells():
+    shape = (5, 6, 7)
+    p = dict(BASE, nx=7, ny=6, nz=5, bc=("periodic", "wall", "wall"))
+    g, o = both(p, np.ones(shape, np.uint8), 6)
+    assert g.info()["fluid_cells"] == 0 and g.info()["boundary_cells"] == 0
+    assert g.ledger()["reacted"] == 0.0
+
+
+@pytest.mark.parametrize("shape", [(1, 9, 40), (5, 1, 40), (5, 9, 1)])
+def test_periodic_axes_one_cell_wide(shape):
+    nz, ny, nx = shape
+    rng = np.random.default_rng(2)
+    mask = (rng.uniform(size=shape) < 0.25).astype(np.uint8)
+    mask.flat[0] = 0
+    assert 0 < mask.sum() < mask.size
+    c0 = 1.0 + 0.2 * rng.standard_normal(shape)
+    p = dict(BASE, nx=nx, ny=ny, nz=nz, bc=("periodic",) * 3)
+    g, o = both(p, mask, 17, c_init=c0)
+    lg, lo = g.ledger(), o.ledger()
+    assert abs(lg["reacted"] - lo["reacted"]) < 1e-9 * max(1.0, abs(lo["reacted"]))
+
+
+@pytest.mark.parametrize("scheme", ["new", "patel_ju", "anti_bb"])
+def test_single_fluid_cell_enclosed(scheme):
+    shape = (5, 5, 5)
+    mask = np.ones(shape, np.uint8)
+    mask[2, 2, 2] = 0
+    p = dict(BASE, nx=5, ny=5, nz=5, bc=("wall",) * 3, scheme=scheme)
+    g, o = both(p, mask, 12)
+    assert g.info()["fluid_cells"] == 1
+    lg, lo = g.ledger(), o.ledger()
+    for k in ("solute", "solid_over_vm", "reacted"):
+        assert abs(lg[k] - lo[k]) < 1e-9 * max(1.0, abs(lo[k])), k
+
+
+def test_pure_solute_lattice_with_walls():
+    shape = (4, 11, 37)
+    rng = np.random.default_rng(3)
+    mask = (rng.uniform(size=shape) < 0.3).astype(np.uint8)
+    p = dict(BASE, nx=37, ny=11, nz=4, flow_q=0, bc=("wall", "periodic", "wall"))
+    both(p, mask, 15, c_init=1.0 + 0.1 * rng.standard_normal(shape))

@@ -75,3 +75,23 @@ def test_batch_domain_handles_are_borrowed():
         lbrbc.lbrbc_step(h, 1)
     b.step(2)
     assert np.isfinite(b.fields(1)[2]).all()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_batch_many_small_domains(precision):
+    # a hundred-odd small domains: the work items of many domains share every
+    # block of the persistent launches, each domain still evolving as it does
+    # alone under every tile policy and order
+    cases, _ = workloads.case_batch(n=110, L_min=9, L_max=16, seed=11, precision=precision)
+    b = lbrbc.Batch(cases)
+    choice = b.autotune(pairs=1)
+    total = 4 * 2 * 3 * 4 + 3
+    b.step(3)
+    for i in range(0, 110, 7):
+        p, mask, init = cases[i]
+        s = lbrbc.Sim(p, mask, **init)
+        s.step(total)
+        tol = 1e-11 if precision == "fp64" else 2e-6
+        for a, c in zip(b.fields(i), s.fields()):
+            assert np.abs(a - c).max() <= tol * max(1.0, np.abs(c).max()), (i, choice)
+        s.close()

@@ -47,6 +47,7 @@ def args_():
                     help="channel: the headline workload; spherepack: 512^3 precipitation with phase change")
     ap.add_argument("--sweep", choices=["dense", "list"], default="dense",
                     help="fluid-cell sweep of the library (LBRBC_FLUID_SWEEP)")
+    ap.add_argument("--domains", type=int, default=256, help="number of domains of --case batch")
     ap.add_argument("--molins-cases", type=str, default="4", help="Table 2 cases of --case molins, e.g. 1,2,3,4")
     ap.add_argument("--scale", type=float, default=1.0, help="resolution of --case molins (1 = the paper's 600x1200)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -359,7 +360,7 @@ def batch_arm(a):
     from paper_2306_10794_gb300 import _build, lbrbc, workloads
 
     _build.build()
-    cases, meta = workloads.case_batch(n=256, precision=a.precision)
+    cases, meta = workloads.case_batch(n=a.domains, precision=a.precision)
     K, W = max(2, a.steps), max(3, a.warmup)
     stream = torch.cuda.current_stream()
     b = lbrbc.Batch(cases)
@@ -393,9 +394,9 @@ def batch_arm(a):
     line = {"metric": METRIC, "value": fluid / (ms_b * 1e-3) / 1e6, "unit": "MLUPS", "n_gpus": 1, "steps": K,
             "warmup": W, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if a.precision == "fp32" else "f64", "data": "synthetic",
-            "config": {"workload": "256 independent 3D dissolution domains, edge U{32..96}, sphere packs porosity "
+            "config": {"workload": "%d independent 3D dissolution domains, edge U{32..96}, sphere packs porosity "
                                    "U[0.3,0.6], Pe log-U[1,1000] (capped to what the lattice reaches), Da "
-                                   "log-U[0.01,10], D3Q19 TRT + D3Q7 TRT, " + a.precision,
+                                   "log-U[0.01,10], D3Q19 TRT + D3Q7 TRT, " % len(cases) + a.precision,
                        "domains": len(cases), "fluid_cells": fluid, "autotune": tune},
             "per_domain_launches": {"ms_per_step": ms_p, "value": fluid / (ms_p * 1e-3) / 1e6, "steps": Kp},
             "batched_speedup": ms_p / ms_b, "clocks": ck,

@@ -403,32 +403,6 @@ class Engine final : public ISim {
         return 0;
     }
 
-    // Same reduction on caller-provided scratch (2 * red_blocks() + 2 doubles).
-    int ledger_with_scratch(double* out, double* part, std::string& err) {
-        LB_CUDA(cudaStreamSynchronize(last_stream_ ? last_stream_ : own_));
-        const int nblk = red_blocks();
-        k_reduce_partial<T, LG><<<nblk, RED_BLOCK, 0, own_>>>(d_, ph_, lastodd_, part);
-        k_reduce_final<0><<<1, 32, 0, own_>>>(part, nblk, part + 2 * nblk);
-        LB_CUDA(cudaGetLastError());
-        double sums[2], acc[4];
-        std::vector<double> bacc((size_t)2 * nbacc_);
-        LB_CUDA(cudaMemcpyAsync(sums, part + 2 * nblk, 2 * sizeof(double), cudaMemcpyDeviceToHost, own_));
-        LB_CUDA(cudaMemcpyAsync(acc, d_.acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, own_));
-        LB_CUDA(cudaMemcpyAsync(bacc.data(), d_.bacc, bacc.size() * sizeof(double), cudaMemcpyDeviceToHost, own_));
-        LB_CUDA(cudaStreamSynchronize(own_));
-        for (int b = 0; b < nbacc_; ++b) {
-            acc[0] += bacc[2 * b];
-            acc[1] += bacc[2 * b + 1];
-        }
-        out[0] = sums[0];
-        out[1] = prm_.molar_volume > 0.0 ? sums[1] / prm_.molar_volume : 0.0;
-        out[2] = acc[2];
-        out[3] = acc[1];
-        out[4] = acc[0];
-        out[5] = (double)steps_;
-        return 0;
-    }
-
     // Mass balance with caller-provided device scratch and no allocation:
     // one partial pair per block of cells_per_block cells, then the final
     // sums; scratch holds 2 * max_blocks + 8 doubles.

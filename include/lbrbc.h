@@ -183,7 +183,7 @@ lbrbc_status lbrbc_mass_ledger_noalloc(lbrbc_sim *sim, double *out);
 lbrbc_status lbrbc_events(lbrbc_sim *sim, int64_t *count, int64_t capacity, int64_t *step, int64_t *node,
                           int32_t *kind);
 
-/* Discrete adjoint (SURVEY "adjoint"; the paper has no gradient): advance
+/* Discrete adjoint (an extension: the paper computes no gradient): advance
  * n_steps >= 1 steps exactly as lbrbc_step would (the simulation ends
  * n_steps later) and return the reacted mass over those steps,
  *   J = sum over steps and reactive links of m_l  (mass injected into the

@@ -2,7 +2,9 @@
 boundary cells at all (an all-fluid periodic box: empty lists, zero
 ledger), no fluid cells at all, periodic axes one cell wide (a cell is its
 own neighbour), a single fluid cell enclosed by reactive solid (every link
-reactive), and a pure solute lattice next to the coupled one."""
+reactive), a pure solute lattice next to the coupled one, and the
+hand-evaluated dissolution events of the oracle's pins (an unpaid charge,
+two simultaneous events sharing a payer)."""
 import numpy as np
 import pytest
 
@@ -91,3 +93,38 @@ def test_pure_solute_lattice_with_walls():
     mask = (rng.uniform(size=shape) < 0.3).astype(np.uint8)
     p = dict(BASE, nx=37, ny=11, nz=4, flow_q=0, bc=("wall", "periodic", "wall"))
     both(p, mask, 15, c_init=1.0 + 0.1 * rng.standard_normal(shape))
+
+
+def _events(x):
+    return x.events().tolist()
+
+
+@pytest.mark.parametrize("case", ["unpaid", "shared_payer"])
+def test_hand_evaluated_dissolution_events_match_oracle(case):
+    # the two phase-change configurations the oracle is pinned on by hand:
+    # an isolated wet cell whose charge goes unpaid, and two simultaneous
+    # dissolutions two cells apart that share a paying solid neighbour
+    Vm = 0.4
+    if case == "unpaid":
+        nx = ny = 5
+        mask = np.zeros((1, ny, nx), np.uint8)
+        mask[0, 2, 2] = 1
+        phi0 = np.where(mask == 1, 1e-12, 0.0)
+        bc = ("periodic", "periodic", "periodic")
+    else:
+        nx, ny = 5, 6
+        mask = np.zeros((1, ny, nx), np.uint8)
+        mask[0, 0:2, :] = 1
+        phi0 = np.where(mask == 1, 1.0, 0.0)
+        phi0[0, 1, 1] = phi0[0, 1, 3] = 1e-12
+        bc = ("periodic", "wall", "periodic")
+    c0 = np.where(mask == 1, 0.0, 0.5)
+    p = dict(dim=2, nx=nx, ny=ny, flow_q=0, solute_q=5, bc=bc, tau_solute=1.0, k_r=0.5, c_eq=1.0, c_init=0.5,
+             molar_volume=Vm, phase_change=1, precision="fp64", event_log_capacity=1024)
+    g, o = both(p, mask, 3, phi_init=phi0, c_init=c0)
+    assert _events(g) == _events(o) and len(_events(o)) == (1 if case == "unpaid" else 2)
+    lg, lo = g.ledger(), o.ledger()
+    for k in ("solute", "solid_over_vm", "unpaid", "reacted"):
+        assert lg[k] == pytest.approx(lo[k], rel=1e-12, abs=1e-13), k
+    if case == "unpaid":
+        assert lo["unpaid"] < 0.0

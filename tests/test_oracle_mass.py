@@ -118,3 +118,75 @@ def test_single_precipitation_event_by_hand():
     assert c[0, 2, 1] == pytest.approx(c_ref[0, 2, 1], rel=1e-14)
     assert c[0, 2, 3] == pytest.approx(c_ref[0, 2, 3], rel=1e-14)
     assert phi[0, 1, 2] == pytest.approx(phi_ref[0, 1, 2] + Vm * c_ref[0, 1, 2], rel=1e-14)
+
+
+def test_dissolution_without_solid_neighbours_is_unpaid_by_hand():
+    """An isolated wet cell that dissolves has no solid neighbour left to pay
+    its charge V_m (C_init - C_b) - phi_b (Sec. 2.4, reading R5): the charge
+    goes to the unpaid ledger term as -charge / V_m, and the new fluid cell
+    takes the mean concentration of its four fluid neighbours.  Expected
+    values are taken from a run without phase change, evaluated by hand."""
+    n, Vm = 5, 0.4
+    mask = np.zeros((1, n, n), np.uint8)
+    mask[0, 2, 2] = 1
+    phi0 = np.where(mask == 1, 1e-12, 0.0)
+    p = dict(dim=2, nx=n, ny=n, flow_q=0, solute_q=5, bc=("periodic", "periodic", "periodic"), tau_solute=1.0,
+             k_r=0.5, c_eq=1.0, c_init=0.5, molar_volume=Vm)
+    c0 = np.where(mask == 1, 0.0, 0.5)  # a solute-free wet cell: its charge is not zero
+    ref = oracle.OracleSim(dict(p, phase_change=0), mask, phi_init=phi0, c_init=c0)
+    ref.step(1)
+    _, _, c_ref, phi_ref = ref.fields()
+    s = oracle.OracleSim(dict(p, phase_change=1), mask, phi_init=phi0, c_init=c0)
+    L0 = s.ledger()
+    s.step(1)
+    assert s.events().tolist() == [[0, 2 + n * 2, oracle.EV_DISSOLVE]]
+    assert (s.classes()[0] == oracle.FLUID).all()
+    _, _, c, phi = s.fields()
+    c_init = np.mean([c_ref[0, 1, 2], c_ref[0, 3, 2], c_ref[0, 2, 1], c_ref[0, 2, 3]])
+    assert c[0, 2, 2] == pytest.approx(c_init, rel=1e-14)
+    assert (phi == 0.0).all()
+    Q = Vm * (c_init - c_ref[0, 2, 2]) - phi_ref[0, 2, 2]
+    assert Q > 0.0
+    L = s.ledger()
+    assert L["unpaid"] == pytest.approx(-Q / Vm, rel=1e-12)
+    assert _invariant(L) == pytest.approx(_invariant(L0), rel=1e-13, abs=1e-13)
+
+
+def test_simultaneous_dissolutions_share_a_payer_by_hand():
+    """Two wet cells two apart on a wall dissolve in the same step.  Events
+    of a step act together on the pre-event state (reading R5): each charge
+    is split equally over its own post-event solid neighbours (including the
+    formerly interior cell below it), and the solid cell between the two
+    pays a third of each charge.  Expected values are taken from a run
+    without phase change, evaluated by hand."""
+    nx, ny, Vm = 5, 6, 0.4
+    mask = np.zeros((1, ny, nx), np.uint8)
+    mask[0, 0:2, :] = 1  # two solid rows; row 1 is the wet boundary row
+    phi0 = np.where(mask == 1, 1.0, 0.0)
+    phi0[0, 1, 1] = phi0[0, 1, 3] = 1e-12
+    c0 = np.where(mask == 1, 0.0, 0.5)  # solute-free wall cells: the charges are not zero
+    p = dict(dim=2, nx=nx, ny=ny, flow_q=0, solute_q=5, bc=("periodic", "wall", "periodic"), tau_solute=1.0,
+             k_r=0.5, c_eq=1.0, c_init=0.5, molar_volume=Vm)
+    ref = oracle.OracleSim(dict(p, phase_change=0), mask, phi_init=phi0, c_init=c0)
+    ref.step(1)
+    _, _, c_ref, phi_ref = ref.fields()
+    s = oracle.OracleSim(dict(p, phase_change=1), mask, phi_init=phi0, c_init=c0)
+    s.step(1)
+    assert s.events().tolist() == [[0, 1 + nx, oracle.EV_DISSOLVE], [0, 3 + nx, oracle.EV_DISSOLVE]]
+    cls = s.classes()[0]
+    assert cls[1, 1] == oracle.FLUID and cls[1, 3] == oracle.FLUID
+    assert cls[0, 1] == oracle.BOUND and cls[0, 3] == oracle.BOUND and cls[1, 2] == oracle.BOUND
+    _, _, c, phi = s.fields()
+    # the only fluid neighbour of each event cell before the events is the cell above it
+    assert c[0, 1, 1] == pytest.approx(c_ref[0, 2, 1], rel=1e-14)
+    assert c[0, 1, 3] == pytest.approx(c_ref[0, 2, 3], rel=1e-14)
+    Q1 = Vm * (c_ref[0, 2, 1] - c_ref[0, 1, 1]) - phi_ref[0, 1, 1]
+    Q3 = Vm * (c_ref[0, 2, 3] - c_ref[0, 1, 3]) - phi_ref[0, 1, 3]
+    assert Q1 > 0.0 and Q3 > 0.0
+    expected = {(1, 0): Q1 / 3, (0, 1): Q1 / 3, (1, 2): Q1 / 3 + Q3 / 3, (1, 4): Q3 / 3, (0, 3): Q3 / 3}
+    for (y, x), q in expected.items():
+        assert phi_ref[0, y, x] - phi[0, y, x] == pytest.approx(q, rel=1e-12), (y, x)
+    # solid cells neither event touches pay nothing
+    for (y, x) in ((0, 0), (0, 2), (0, 4)):
+        assert phi[0, y, x] == phi_ref[0, y, x]
+    assert phi[0, 1, 1] == 0.0 and phi[0, 1, 3] == 0.0

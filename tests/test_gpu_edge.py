@@ -99,30 +99,44 @@ def _events(x):
     return x.events().tolist()
 
 
-@pytest.mark.parametrize("case", ["unpaid", "shared_payer"])
-def test_hand_evaluated_dissolution_events_match_oracle(case):
-    # the two phase-change configurations the oracle is pinned on by hand:
-    # an isolated wet cell whose charge goes unpaid, and two simultaneous
-    # dissolutions two cells apart that share a paying solid neighbour
+@pytest.mark.parametrize("case", ["unpaid", "shared_payer", "adjacent", "enclosed_precipitation"])
+def test_hand_evaluated_phase_change_events_match_oracle(case):
+    # the phase-change configurations the oracle is pinned on by hand: an
+    # isolated wet cell whose charge goes unpaid, two simultaneous
+    # dissolutions two cells apart sharing a paying neighbour, two adjacent
+    # simultaneous dissolutions, and a precipitation left with no fluid
+    # neighbour
     Vm = 0.4
+    c_init, c_eq, bc = 0.5, 1.0, ("periodic", "wall", "periodic")
     if case == "unpaid":
         nx = ny = 5
         mask = np.zeros((1, ny, nx), np.uint8)
         mask[0, 2, 2] = 1
         phi0 = np.where(mask == 1, 1e-12, 0.0)
-        bc = ("periodic", "periodic", "periodic")
+        bc = ("periodic",) * 3
+        n_ev = 1
+    elif case == "enclosed_precipitation":
+        nx = ny = 5
+        mask = np.ones((1, ny, nx), np.uint8)
+        mask[0, 2, 2] = 0
+        phi0 = np.where(mask == 1, 1.0, 1.0 - 1e-12)
+        c_init, c_eq, bc = 1.0, 0.0, ("periodic",) * 3
+        n_ev = 1
     else:
-        nx, ny = 5, 6
+        nx, ny = (5, 6) if case == "shared_payer" else (6, 6)
         mask = np.zeros((1, ny, nx), np.uint8)
         mask[0, 0:2, :] = 1
         phi0 = np.where(mask == 1, 1.0, 0.0)
-        phi0[0, 1, 1] = phi0[0, 1, 3] = 1e-12
-        bc = ("periodic", "wall", "periodic")
-    c0 = np.where(mask == 1, 0.0, 0.5)
-    p = dict(dim=2, nx=nx, ny=ny, flow_q=0, solute_q=5, bc=bc, tau_solute=1.0, k_r=0.5, c_eq=1.0, c_init=0.5,
+        cells = (1, 3) if case == "shared_payer" else (2, 3)
+        phi0[0, 1, cells[0]] = phi0[0, 1, cells[1]] = 1e-12
+        n_ev = 2
+    init = dict(phi_init=phi0)
+    if case != "enclosed_precipitation":
+        init["c_init"] = np.where(mask == 1, 0.0, 0.5)
+    p = dict(dim=2, nx=nx, ny=ny, flow_q=0, solute_q=5, bc=bc, tau_solute=1.0, k_r=0.5, c_eq=c_eq, c_init=c_init,
              molar_volume=Vm, phase_change=1, precision="fp64", event_log_capacity=1024)
-    g, o = both(p, mask, 3, phi_init=phi0, c_init=c0)
-    assert _events(g) == _events(o) and len(_events(o)) == (1 if case == "unpaid" else 2)
+    g, o = both(p, mask, 3, **init)
+    assert _events(g) == _events(o) and len(_events(o)) == n_ev
     lg, lo = g.ledger(), o.ledger()
     for k in ("solute", "solid_over_vm", "unpaid", "reacted"):
         assert lg[k] == pytest.approx(lo[k], rel=1e-12, abs=1e-13), k

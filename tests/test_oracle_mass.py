@@ -190,3 +190,60 @@ def test_simultaneous_dissolutions_share_a_payer_by_hand():
     for (y, x) in ((0, 0), (0, 2), (0, 4)):
         assert phi[0, y, x] == phi_ref[0, y, x]
     assert phi[0, 1, 1] == 0.0 and phi[0, 1, 3] == 0.0
+
+
+def test_adjacent_simultaneous_dissolutions_by_hand():
+    """Two neighbouring wet cells dissolve in the same step (reading R5:
+    events act together on the pre-event state).  Neither counts the other
+    as a fluid neighbour when it takes its concentration, and neither pays
+    the other's charge (both are fluid after the events): each charge is
+    split over the other two solid neighbours only."""
+    nx, ny, Vm = 6, 6, 0.4
+    mask = np.zeros((1, ny, nx), np.uint8)
+    mask[0, 0:2, :] = 1
+    phi0 = np.where(mask == 1, 1.0, 0.0)
+    phi0[0, 1, 2] = phi0[0, 1, 3] = 1e-12
+    c0 = np.where(mask == 1, 0.0, 0.5)
+    p = dict(dim=2, nx=nx, ny=ny, flow_q=0, solute_q=5, bc=("periodic", "wall", "periodic"), tau_solute=1.0,
+             k_r=0.5, c_eq=1.0, c_init=0.5, molar_volume=Vm)
+    ref = oracle.OracleSim(dict(p, phase_change=0), mask, phi_init=phi0, c_init=c0)
+    ref.step(1)
+    _, _, c_ref, phi_ref = ref.fields()
+    s = oracle.OracleSim(dict(p, phase_change=1), mask, phi_init=phi0, c_init=c0)
+    s.step(1)
+    assert s.events().tolist() == [[0, 2 + nx, oracle.EV_DISSOLVE], [0, 3 + nx, oracle.EV_DISSOLVE]]
+    _, _, c, phi = s.fields()
+    assert c[0, 1, 2] == pytest.approx(c_ref[0, 2, 2], rel=1e-14)
+    assert c[0, 1, 3] == pytest.approx(c_ref[0, 2, 3], rel=1e-14)
+    Q2 = Vm * (c_ref[0, 2, 2] - c_ref[0, 1, 2]) - phi_ref[0, 1, 2]
+    Q3 = Vm * (c_ref[0, 2, 3] - c_ref[0, 1, 3]) - phi_ref[0, 1, 3]
+    expected = {(1, 1): Q2 / 2, (0, 2): Q2 / 2, (1, 4): Q3 / 2, (0, 3): Q3 / 2}
+    for (y, x), q in expected.items():
+        assert phi_ref[0, y, x] - phi[0, y, x] == pytest.approx(q, rel=1e-12), (y, x)
+    assert phi[0, 1, 2] == 0.0 and phi[0, 1, 3] == 0.0
+
+
+def test_precipitation_without_fluid_neighbours_by_hand():
+    """A fluid cell enclosed by reactive solid precipitates (reading R5): with
+    no fluid neighbour after the event there is nowhere to send the excess,
+    so the cell keeps phi + V_m C (above 1) and its solute is removed; the
+    balance sum C + sum phi / V_m is unchanged by the event."""
+    n, Vm = 5, 0.4
+    mask = np.ones((1, n, n), np.uint8)
+    mask[0, 2, 2] = 0
+    phi0 = np.where(mask == 1, 1.0, 1.0 - 1e-12)
+    p = dict(dim=2, nx=n, ny=n, flow_q=0, solute_q=5, bc=("periodic", "periodic", "periodic"), tau_solute=1.0,
+             k_r=0.5, c_eq=0.0, c_init=1.0, molar_volume=Vm)
+    ref = oracle.OracleSim(dict(p, phase_change=0), mask, phi_init=phi0)
+    ref.step(1)
+    _, _, c_ref, phi_ref = ref.fields()
+    L_ref = ref.ledger()
+    s = oracle.OracleSim(dict(p, phase_change=1), mask, phi_init=phi0)
+    s.step(1)
+    assert s.events().tolist() == [[0, 2 + n * 2, oracle.EV_PRECIPITATE]]
+    assert (s.classes()[0] == oracle.SOLID).all()
+    _, _, c, phi = s.fields()
+    assert phi[0, 2, 2] == pytest.approx(phi_ref[0, 2, 2] + Vm * c_ref[0, 2, 2], rel=1e-14)
+    assert phi[0, 2, 2] > 1.0 and c[0, 2, 2] == 0.0
+    L = s.ledger()
+    assert _invariant(L) == pytest.approx(_invariant(L_ref), rel=1e-13)

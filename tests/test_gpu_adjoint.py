@@ -95,6 +95,6 @@ def test_torch_autograd_wrapper():
     J.backward()
     sim = lbrbc.Sim(dict(p, c_eq=1.0), mask, k_field=kf.detach().numpy())
     J2, dk, dc, g = sim.adjoint(40, field=True)
-    assert float(J) == pytest.approx(J2, rel=1e-13)
+    assert float(J.detach()) == pytest.approx(J2, rel=1e-13)
     assert np.allclose(kf.grad.numpy(), g, rtol=1e-12, atol=0)
     assert float(ceq.grad) == pytest.approx(dc, rel=1e-12)

@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(FLUID_BLOCK) k_adj_fluid(const Dev<T> a, const
 // dk: per-cell dJ/dk_r (FP64, may be null); part: per-block partials of the
 // scalar dJ/dk_r and dJ/dc_eq (FP64, accumulated over steps).
 template <typename T, class LG>
-__global__ void __launch_bounds__(LIST_BLOCK) k_adj_bound(const Dev<T> a, const Phys p, const PhysT<T> q,
+__global__ void __launch_bounds__(LIST_BLOCK, 4) k_adj_bound(const Dev<T> a, const Phys p, const PhysT<T> q,
                                                          const T* __restrict__ lam, T* __restrict__ nu,
                                                          const T* __restrict__ gprev, double* __restrict__ dk,
                                                          double* __restrict__ part) {

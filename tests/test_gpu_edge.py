@@ -99,13 +99,13 @@ def _events(x):
     return x.events().tolist()
 
 
-@pytest.mark.parametrize("case", ["unpaid", "shared_payer", "adjacent", "enclosed_precipitation"])
+@pytest.mark.parametrize("case", ["unpaid", "shared_payer", "adjacent", "enclosed_precipitation", "mixed"])
 def test_hand_evaluated_phase_change_events_match_oracle(case):
     # the phase-change configurations the oracle is pinned on by hand: an
     # isolated wet cell whose charge goes unpaid, two simultaneous
     # dissolutions two cells apart sharing a paying neighbour, two adjacent
-    # simultaneous dissolutions, and a precipitation left with no fluid
-    # neighbour
+    # simultaneous dissolutions, a precipitation left with no fluid
+    # neighbour, and a dissolution and a precipitation in the same step
     Vm = 0.4
     c_init, c_eq, bc = 0.5, 1.0, ("periodic", "wall", "periodic")
     if case == "unpaid":
@@ -115,6 +115,15 @@ def test_hand_evaluated_phase_change_events_match_oracle(case):
         phi0 = np.where(mask == 1, 1e-12, 0.0)
         bc = ("periodic",) * 3
         n_ev = 1
+    elif case == "mixed":
+        nx, ny = 8, 6
+        mask = np.zeros((1, ny, nx), np.uint8)
+        mask[0, 0:2, :] = 1
+        phi0 = np.where(mask == 1, 1.0, 0.0)
+        phi0[0, 1, 1] = 1e-12
+        phi0[0, 2, 5] = 1.0 - 1e-12
+        c_eq = 0.5
+        n_ev = 2
     elif case == "enclosed_precipitation":
         nx = ny = 5
         mask = np.ones((1, ny, nx), np.uint8)
@@ -131,7 +140,11 @@ def test_hand_evaluated_phase_change_events_match_oracle(case):
         phi0[0, 1, cells[0]] = phi0[0, 1, cells[1]] = 1e-12
         n_ev = 2
     init = dict(phi_init=phi0)
-    if case != "enclosed_precipitation":
+    if case == "mixed":
+        c0 = np.zeros((1, ny, nx))
+        c0[0, :, 4:] = 1.0
+        init["c_init"] = c0
+    elif case != "enclosed_precipitation":
         init["c_init"] = np.where(mask == 1, 0.0, 0.5)
     p = dict(dim=2, nx=nx, ny=ny, flow_q=0, solute_q=5, bc=bc, tau_solute=1.0, k_r=0.5, c_eq=c_eq, c_init=c_init,
              molar_volume=Vm, phase_change=1, precision="fp64", event_log_capacity=1024)

@@ -247,3 +247,47 @@ def test_precipitation_without_fluid_neighbours_by_hand():
     assert phi[0, 2, 2] > 1.0 and c[0, 2, 2] == 0.0
     L = s.ledger()
     assert _invariant(L) == pytest.approx(_invariant(L_ref), rel=1e-13)
+
+
+def test_dissolution_and_precipitation_in_one_step_by_hand():
+    """A wall under a solute-free column dissolves at one cell while a bump
+    grows on it under a supersaturated column, in the same step (reading R5:
+    every event of a step follows its own rule on the pre-event state).  The
+    dissolving cell takes the concentration of the cell above it and charges
+    its three solid neighbours; the precipitating cell keeps phi := 1 and
+    sends its whole excess up (the flat-wall normal, as in
+    test_single_precipitation_event_by_hand), and the wall cell under it,
+    left without a fluid neighbour, turns its solute into phi."""
+    nx, ny, Vm = 8, 6, 0.4
+    mask = np.zeros((1, ny, nx), np.uint8)
+    mask[0, 0:2, :] = 1
+    phi0 = np.where(mask == 1, 1.0, 0.0)
+    phi0[0, 1, 1] = 1e-12        # dissolves
+    phi0[0, 2, 5] = 1.0 - 1e-12  # precipitates
+    c0 = np.zeros((1, ny, nx))
+    c0[0, :, 4:] = 1.0           # supersaturated columns x >= 4, solute-free columns x < 4 (c_eq = 0.5)
+    p = dict(dim=2, nx=nx, ny=ny, flow_q=0, solute_q=5, bc=("periodic", "wall", "periodic"), tau_solute=1.0,
+             k_r=0.5, c_eq=0.5, c_init=0.5, molar_volume=Vm)
+    ref = oracle.OracleSim(dict(p, phase_change=0), mask, phi_init=phi0, c_init=c0)
+    ref.step(1)
+    _, _, c_ref, phi_ref = ref.fields()
+    s = oracle.OracleSim(dict(p, phase_change=1), mask, phi_init=phi0, c_init=c0)
+    L0 = s.ledger()
+    s.step(1)
+    assert s.events().tolist() == [[0, 1 + nx, oracle.EV_DISSOLVE], [0, 5 + 2 * nx, oracle.EV_PRECIPITATE]]
+    _, _, c, phi = s.fields()
+    # dissolution
+    assert c[0, 1, 1] == pytest.approx(c_ref[0, 2, 1], rel=1e-14)
+    Q = Vm * (c_ref[0, 2, 1] - c_ref[0, 1, 1]) - phi_ref[0, 1, 1]
+    for (y, x) in ((1, 0), (1, 2), (0, 1)):
+        assert phi_ref[0, y, x] - phi[0, y, x] == pytest.approx(Q / 3, rel=1e-12), (y, x)
+    assert phi[0, 1, 1] == 0.0
+    # precipitation
+    excess = phi_ref[0, 2, 5] + Vm * c_ref[0, 2, 5] - 1.0
+    assert excess > 0.0
+    assert phi[0, 2, 5] == 1.0 and c[0, 2, 5] == 0.0
+    assert c[0, 3, 5] == pytest.approx(c_ref[0, 3, 5] + excess / Vm, rel=1e-14)
+    assert c[0, 2, 4] == pytest.approx(c_ref[0, 2, 4], rel=1e-14)
+    assert c[0, 2, 6] == pytest.approx(c_ref[0, 2, 6], rel=1e-14)
+    assert phi[0, 1, 5] == pytest.approx(phi_ref[0, 1, 5] + Vm * c_ref[0, 1, 5], rel=1e-14)
+    assert _invariant(s.ledger()) == pytest.approx(_invariant(L0), rel=1e-13)

@@ -166,15 +166,25 @@ lbrbc_status lbrbc_mass_ledger(lbrbc_sim *sim, double *out);
  *     present on every GPU that loads the library until the process exits.
  *     Partial sums are kept per block of 65536 cells, so grids above
  *     4096 * 65536 = 268435456 cells are rejected with LBRBC_ERR_ARG.
- *   - The first call on a device looks up the array's device address (with
- *     the simulation's device made current); make that first call before any
- *     stream capture.
+ *   - Every call looks up the array's device address with the simulation's
+ *     device made current (nothing is cached, so a device reset between
+ *     calls is harmless).
  *   - Every call on a device shares the array and leaves its last contents
  *     there; each call overwrites every entry it reads, so nothing needs
  *     clearing.  Calls that overlap on the GPU (two host threads, two
  *     simulations on one device at once) race on it: serialise them.
  *   - Synchronises the stream of the last lbrbc_step.  `out`: host, 6 doubles. */
 lbrbc_status lbrbc_mass_ledger_noalloc(lbrbc_sim *sim, double *out);
+
+/* The size rule of lbrbc_mass_ledger_noalloc on its own (host arithmetic,
+ * no GPU needed; the paper has no counterpart): a grid of n_cells cells needs
+ * ceil(n_cells / cells_per_block) partial pairs and fits if that is at most
+ * max_blocks.  lbrbc_mass_ledger_noalloc applies it with max_blocks = 4096
+ * and cells_per_block = 65536.  Returns LBRBC_OK, or LBRBC_ERR_ARG with the
+ * reason (naming the cell limit) written to msg (host, msg_len bytes,
+ * NUL-terminated; may be NULL). */
+lbrbc_status lbrbc_noalloc_size_check(int64_t n_cells, int32_t max_blocks, int64_t cells_per_block, char *msg,
+                                      int32_t msg_len);
 
 /* Phase-change events logged so far (up to event_log_capacity): on return
  * *count holds the number logged; if step/node/kind are non-NULL the first

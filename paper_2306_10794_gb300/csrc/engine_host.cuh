@@ -408,12 +408,8 @@ class Engine final : public ISim {
     // sums; scratch holds 2 * max_blocks + 8 doubles.
     int ledger_scratch(double* out, double* scratch, int max_blocks, long long cells_per_block,
                        std::string& err) override {
+        if (int rc = noalloc_size_check(ncell_, max_blocks, cells_per_block, err)) return rc;
         const long long nblk = (ncell_ + cells_per_block - 1) / cells_per_block;
-        if (nblk > max_blocks) {
-            err = "grid of " + std::to_string(ncell_) + " cells exceeds the static scratch of this entry point (" +
-                  std::to_string((long long)max_blocks * cells_per_block) + " cells)";
-            return 1;
-        }
         LB_CUDA(cudaStreamSynchronize(last_stream_ ? last_stream_ : own_));
         double* tail = scratch + 2 * (size_t)max_blocks;
         k_reduce_partial<T, LG><<<(int)nblk, RED_BLOCK, 0, own_>>>(d_, ph_, lastodd_, scratch);

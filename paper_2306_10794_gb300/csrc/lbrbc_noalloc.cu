@@ -4,7 +4,8 @@
 // declaration in include/lbrbc.h for the contract).
 #include <cuda_runtime.h>
 
-#include <mutex>
+#include <algorithm>
+#include <cstring>
 #include <string>
 
 #include "sim_iface.h"
@@ -18,29 +19,19 @@ namespace {
 // held by every GPU that loads the library until the process exits.
 static __device__ __align__(256) double g_ledger_scratch[2 * LBRBC_NOALLOC_MAX_BLOCKS + 8];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on `dev`, looked up once per device
-// with that device current.  In host code the array's name is only a
-// host-side stand-in, so kernels are always given this address.
-int scratch_on(int dev, double** out, std::string& err) {
-    if (dev < 0 || dev >= kMaxDevices) {
-        err = "device index out of range for the static ledger scratch";
-        return LBRBC_ERR_ARG;
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a host-side stand-in, so kernels are always given
+// this address.  It is looked up on every call (no cache): after a device
+// reset or a new primary context the module is reloaded and the array may
+// move, and the lookup costs little next to the call's stream synchronisation.
+int scratch_here(double** out, std::string& err) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_ledger_scratch);
+    if (e != cudaSuccess) {
+        err = std::string("cudaGetSymbolAddress(static ledger scratch): ") + cudaGetErrorString(e);
+        return LBRBC_ERR_CUDA;
     }
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_ledger_scratch);
-        if (e != cudaSuccess) {
-            err = std::string("cudaGetSymbolAddress(static ledger scratch): ") + cudaGetErrorString(e);
-            return LBRBC_ERR_CUDA;
-        }
-        g_scratch_addr[dev] = (double*)p;
-    }
-    *out = g_scratch_addr[dev];
+    *out = (double*)p;
     return LBRBC_OK;
 }
 
@@ -64,10 +55,22 @@ extern "C" lbrbc_status lbrbc_mass_ledger_noalloc(lbrbc_sim* sim, double* out) {
     }
     std::string err;
     double* scratch = nullptr;
-    int rc = scratch_on(sim->device, &scratch, err);
+    int rc = scratch_here(&scratch, err);
     if (rc == LBRBC_OK)
         rc = sim->impl->ledger_scratch(out, scratch, LBRBC_NOALLOC_MAX_BLOCKS, LBRBC_NOALLOC_CELLS_PER_BLOCK, err);
     if (cur != sim->device) cudaSetDevice(cur);
     if (rc != LBRBC_OK) sim->err = err;
+    return (lbrbc_status)rc;
+}
+
+extern "C" lbrbc_status lbrbc_noalloc_size_check(int64_t n_cells, int32_t max_blocks, int64_t cells_per_block,
+                                                 char* msg, int32_t msg_len) {
+    std::string err;
+    const int rc = lbrbc::noalloc_size_check((long long)n_cells, (int)max_blocks, (long long)cells_per_block, err);
+    if (msg && msg_len > 0) {
+        const size_t n = std::min<size_t>(err.size(), (size_t)msg_len - 1);
+        memcpy(msg, err.data(), n);
+        msg[n] = '\0';
+    }
     return (lbrbc_status)rc;
 }

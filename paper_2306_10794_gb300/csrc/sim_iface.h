@@ -45,6 +45,24 @@ class IBatch {
     virtual long long fluid_cells() const = 0;
 };
 
+// Size rule of the scratch-based ledger: one partial pair per block of
+// cells_per_block cells, at most max_blocks blocks.  Returns LBRBC_OK or
+// LBRBC_ERR_ARG with a message naming the limit.
+inline int noalloc_size_check(long long ncell, int max_blocks, long long cells_per_block, std::string& err) {
+    if (ncell < 0 || max_blocks < 1 || cells_per_block < 1) {
+        err = "invalid size arguments";
+        return LBRBC_ERR_ARG;
+    }
+    const long long nblk = (ncell + cells_per_block - 1) / cells_per_block;
+    if (nblk > max_blocks) {
+        err = "grid of " + std::to_string(ncell) + " cells exceeds the static scratch of this entry point (" +
+              std::to_string((long long)max_blocks * cells_per_block) + " cells)";
+        return LBRBC_ERR_ARG;
+    }
+    err.clear();
+    return LBRBC_OK;
+}
+
 // Factories, one per translation unit; nullptr if the combination is not built.
 ISim* make_sim_3d(int precision, int flow_q, int solute_q);
 ISim* make_sim_2d(int precision, int flow_q, int solute_q);

@@ -54,7 +54,7 @@ class LbrbcError(RuntimeError):
 _lib = None
 
 EXPORTED = ["lbrbc_create", "lbrbc_step", "lbrbc_fields", "lbrbc_classes", "lbrbc_mass_ledger",
-            "lbrbc_mass_ledger_noalloc",
+            "lbrbc_mass_ledger_noalloc", "lbrbc_noalloc_size_check",
             "lbrbc_events", "lbrbc_adjoint", "lbrbc_profile_step", "lbrbc_info", "lbrbc_check", "lbrbc_last_error",
             "lbrbc_destroy", "lbrbc_batch_create", "lbrbc_batch_step", "lbrbc_batch_autotune",
             "lbrbc_batch_info", "lbrbc_batch_domain", "lbrbc_batch_last_error", "lbrbc_batch_destroy"]
@@ -82,6 +82,9 @@ def load(path: str = LIB_PATH):
     lib.lbrbc_mass_ledger.argtypes = [vp, dp]
     lib.lbrbc_mass_ledger_noalloc.restype = ctypes.c_int
     lib.lbrbc_mass_ledger_noalloc.argtypes = [vp, dp]
+    lib.lbrbc_noalloc_size_check.restype = ctypes.c_int
+    lib.lbrbc_noalloc_size_check.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, ctypes.c_char_p,
+                                             ctypes.c_int32]
     lib.lbrbc_events.restype = ctypes.c_int
     lib.lbrbc_events.argtypes = [vp, P(ctypes.c_int64), ctypes.c_int64, P(ctypes.c_int64), P(ctypes.c_int64),
                                  P(ctypes.c_int32)]
@@ -168,6 +171,14 @@ def lbrbc_mass_ledger_noalloc(handle):
     out = np.zeros(6)
     _check(lib, handle, lib.lbrbc_mass_ledger_noalloc(handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return out
+
+
+def lbrbc_noalloc_size_check(n_cells: int, max_blocks: int = 4096, cells_per_block: int = 65536):
+    """(status, message) of the size rule of lbrbc_mass_ledger_noalloc (host only)."""
+    lib = load()
+    buf = ctypes.create_string_buffer(256)
+    st = lib.lbrbc_noalloc_size_check(int(n_cells), int(max_blocks), int(cells_per_block), buf, len(buf))
+    return st, buf.value.decode()
 
 
 def lbrbc_events(handle):

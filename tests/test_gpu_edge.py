@@ -155,3 +155,52 @@ def test_hand_evaluated_phase_change_events_match_oracle(case):
         assert lg[k] == pytest.approx(lo[k], rel=1e-12, abs=1e-13), k
     if case == "unpaid":
         assert lo["unpaid"] < 0.0
+
+
+@pytest.mark.parametrize("case", ["bulk_precipitations", "wall_precipitations", "dirichlet_neighbour",
+                                  "inlet_face"])
+def test_hand_evaluated_events_near_other_boundaries_match_oracle(case):
+    # the further configurations the oracle is pinned on by hand: two
+    # precipitations sharing a fluid neighbour (open fluid: equal split;
+    # flat wall: nothing sideways), a dissolution above a Dirichlet cell,
+    # and a dissolution on the inlet face
+    Vm = 0.4
+    p = dict(dim=2, flow_q=0, solute_q=5, tau_solute=1.0, k_r=0.5, molar_volume=Vm, phase_change=1,
+             precision="fp64", event_log_capacity=1024)
+    init = {}
+    if case == "bulk_precipitations":
+        nx, ny = 7, 5
+        mask = np.zeros((1, ny, nx), np.uint8)
+        phi0 = np.zeros((1, ny, nx))
+        phi0[0, 2, 2] = phi0[0, 2, 4] = 1.0
+        p.update(bc=("periodic",) * 3, c_eq=0.0, c_init=0.8)
+    elif case == "wall_precipitations":
+        nx, ny = 5, 6
+        mask = np.zeros((1, ny, nx), np.uint8)
+        mask[0, 0:2, :] = 1
+        phi0 = np.where(mask == 1, 1.0, 0.0)
+        phi0[0, 2, 1] = phi0[0, 2, 3] = 1.0 - 1e-12
+        p.update(bc=("periodic", "wall", "periodic"), c_eq=0.0, c_init=1.0)
+    elif case == "dirichlet_neighbour":
+        nx, ny = 5, 6
+        mask = np.zeros((1, ny, nx), np.uint8)
+        mask[0, 0:2, :] = 1
+        mask[0, 0, 2] = 2
+        phi0 = np.where(mask == 1, 1.0, 0.0)
+        phi0[0, 1, 2] = 1e-12
+        init["c_init"] = np.where(mask == 0, 0.5, 0.0)
+        p.update(bc=("periodic", "wall", "periodic"), c_eq=1.0, c_init=0.5, c_dirichlet=0.7)
+    else:
+        nx, ny = 6, 6
+        mask = np.zeros((1, ny, nx), np.uint8)
+        mask[0, 0:2, :] = 1
+        phi0 = np.where(mask == 1, 1.0, 0.0)
+        phi0[0, 1, 0] = 1e-12
+        init["c_init"] = np.where(mask == 0, 0.5, 0.0)
+        p.update(bc=("open", "wall", "periodic"), c_eq=1.0, c_init=0.5, c_inlet=0.9)
+    p.update(nx=nx, ny=ny)
+    g, o = both(p, mask, 6, phi_init=phi0, **init)
+    assert _events(g) == _events(o) and len(_events(o)) >= 1
+    lg, lo = g.ledger(), o.ledger()
+    for k in ("solute", "solid_over_vm", "unpaid", "dirichlet_in", "reacted"):
+        assert lg[k] == pytest.approx(lo[k], rel=1e-12, abs=1e-13), k

@@ -291,3 +291,127 @@ def test_dissolution_and_precipitation_in_one_step_by_hand():
     assert c[0, 2, 6] == pytest.approx(c_ref[0, 2, 6], rel=1e-14)
     assert phi[0, 1, 5] == pytest.approx(phi_ref[0, 1, 5] + Vm * c_ref[0, 1, 5], rel=1e-14)
     assert _invariant(s.ledger()) == pytest.approx(_invariant(L0), rel=1e-13)
+
+
+def test_simultaneous_precipitations_share_a_fluid_neighbour_by_hand():
+    """Two fluid cells two apart reach phi = 1 in the same step (reading R5).
+    In open fluid the solid indicator around each new solid cell is zero, so
+    its normal is undefined, every link counts as aligned, and its excess
+    V_m C goes to its four fluid neighbours in equal shares; the cell between
+    the two receives a share from each.  On a flat wall the same pair sends
+    its whole excess up along the wall normal and the cell between them
+    receives nothing.  Expected values are taken from a run without phase
+    change, evaluated by hand."""
+    n, Vm = 7, 0.4
+    mask = np.zeros((1, 5, n), np.uint8)
+    phi0 = np.zeros((1, 5, n))
+    phi0[0, 2, 2] = phi0[0, 2, 4] = 1.0
+    p = dict(dim=2, nx=n, ny=5, flow_q=0, solute_q=5, bc=("periodic",) * 3, tau_solute=1.0, k_r=0.5, c_eq=0.0,
+             c_init=0.8, molar_volume=Vm)
+    ref = oracle.OracleSim(dict(p, phase_change=0), mask, phi_init=phi0)
+    ref.step(1)
+    _, _, c_ref, phi_ref = ref.fields()
+    s = oracle.OracleSim(dict(p, phase_change=1), mask, phi_init=phi0)
+    L0 = s.ledger()
+    s.step(1)
+    assert s.events().tolist() == [[0, 2 + 2 * n, oracle.EV_PRECIPITATE], [0, 4 + 2 * n, oracle.EV_PRECIPITATE]]
+    _, _, c, phi = s.fields()
+    share = {x: (phi_ref[0, 2, x] + Vm * c_ref[0, 2, x] - 1.0) / Vm / 4.0 for x in (2, 4)}
+    assert share[2] > 0.0 and share[4] > 0.0
+    assert c[0, 2, 3] == pytest.approx(c_ref[0, 2, 3] + share[2] + share[4], rel=1e-14)
+    for (y, x), src in {(2, 1): 2, (1, 2): 2, (3, 2): 2, (2, 5): 4, (1, 4): 4, (3, 4): 4}.items():
+        assert c[0, y, x] == pytest.approx(c_ref[0, y, x] + share[src], rel=1e-14), (y, x)
+    for x in (2, 4):
+        assert phi[0, 2, x] == 1.0 and c[0, 2, x] == 0.0
+    assert _invariant(s.ledger()) == pytest.approx(_invariant(L0), rel=1e-13)
+
+    # the same pair as bumps on a flat wall
+    nx, ny = 5, 6
+    mask = np.zeros((1, ny, nx), np.uint8)
+    mask[0, 0:2, :] = 1
+    phi0 = np.where(mask == 1, 1.0, 0.0)
+    phi0[0, 2, 1] = phi0[0, 2, 3] = 1.0 - 1e-12
+    p = dict(p, nx=nx, ny=ny, bc=("periodic", "wall", "periodic"), c_init=1.0)
+    ref = oracle.OracleSim(dict(p, phase_change=0), mask, phi_init=phi0)
+    ref.step(1)
+    _, _, c_ref, phi_ref = ref.fields()
+    s = oracle.OracleSim(dict(p, phase_change=1), mask, phi_init=phi0)
+    s.step(1)
+    assert len(s.events()) == 2
+    _, _, c, phi = s.fields()
+    assert c[0, 2, 2] == pytest.approx(c_ref[0, 2, 2], rel=1e-14)
+    for x in (1, 3):
+        excess = phi_ref[0, 2, x] + Vm * c_ref[0, 2, x] - 1.0
+        assert c[0, 3, x] == pytest.approx(c_ref[0, 3, x] + excess / Vm, rel=1e-14)
+
+
+def test_dissolution_next_to_a_dirichlet_cell_by_hand():
+    """A wet cell above a Dirichlet cell dissolves (reading R5): only the
+    reactive solid neighbours pay its charge (here two, half each); the
+    Dirichlet cell, which gains a fluid neighbour, becomes a boundary cell
+    holding C = 0 and pays nothing.  The balance, which books what Dirichlet
+    cells inject, is unchanged through the event and after it."""
+    nx, ny, Vm = 5, 6, 0.4
+    mask = np.zeros((1, ny, nx), np.uint8)
+    mask[0, 0:2, :] = 1
+    mask[0, 0, 2] = 2  # Dirichlet cell under the dissolving one
+    phi0 = np.where(mask == 1, 1.0, 0.0)
+    phi0[0, 1, 2] = 1e-12
+    c0 = np.where(mask == 0, 0.5, 0.0)
+    p = dict(dim=2, nx=nx, ny=ny, flow_q=0, solute_q=5, bc=("periodic", "wall", "periodic"), tau_solute=1.0,
+             k_r=0.5, c_eq=1.0, c_init=0.5, c_dirichlet=0.7, molar_volume=Vm)
+    ref = oracle.OracleSim(dict(p, phase_change=0), mask, phi_init=phi0, c_init=c0)
+    ref.step(1)
+    _, _, c_ref, phi_ref = ref.fields()
+    s = oracle.OracleSim(dict(p, phase_change=1), mask, phi_init=phi0, c_init=c0)
+    L0 = s.ledger()
+    s.step(1)
+    assert s.events().tolist() == [[0, 2 + nx, oracle.EV_DISSOLVE]]
+    cls = s.classes()[0]
+    assert cls[1, 2] == oracle.FLUID and cls[0, 2] == oracle.BOUND
+    _, _, c, phi = s.fields()
+    assert c[0, 1, 2] == pytest.approx(c_ref[0, 2, 2], rel=1e-14)
+    assert c[0, 0, 2] == 0.0 and phi[0, 0, 2] == phi_ref[0, 0, 2]
+    Q = Vm * (c_ref[0, 2, 2] - c_ref[0, 1, 2]) - phi_ref[0, 1, 2]
+    assert Q > 0.0
+    for x in (1, 3):
+        assert phi_ref[0, 1, x] - phi[0, 1, x] == pytest.approx(Q / 2, rel=1e-12), x
+    assert _invariant(s.ledger()) == pytest.approx(_invariant(L0), rel=1e-13)
+    s.step(5)
+    assert s.ledger()["dirichlet_in"] != L0["dirichlet_in"]
+    assert _invariant(s.ledger()) == pytest.approx(_invariant(L0), rel=1e-13)
+
+
+def test_dissolution_at_the_inlet_face_by_hand():
+    """A wet cell on the inlet face x = 0 dissolves (reading R5 with the open
+    boundary of reading R9): the inlet is not a cell, so the new fluid cell
+    takes the concentration of its one fluid neighbour and its charge is
+    split over its two reactive solid neighbours; from the next step on its
+    inlet link injects solute, booked in the open-boundary term."""
+    nx, ny, Vm = 6, 6, 0.4
+    mask = np.zeros((1, ny, nx), np.uint8)
+    mask[0, 0:2, :] = 1
+    phi0 = np.where(mask == 1, 1.0, 0.0)
+    phi0[0, 1, 0] = 1e-12
+    c0 = np.where(mask == 0, 0.5, 0.0)
+    p = dict(dim=2, nx=nx, ny=ny, flow_q=0, solute_q=5, bc=("open", "wall", "periodic"), tau_solute=1.0, k_r=0.5,
+             c_eq=1.0, c_init=0.5, c_inlet=0.9, molar_volume=Vm)
+    ref = oracle.OracleSim(dict(p, phase_change=0), mask, phi_init=phi0, c_init=c0)
+    ref.step(1)
+    _, _, c_ref, phi_ref = ref.fields()
+    s = oracle.OracleSim(dict(p, phase_change=1), mask, phi_init=phi0, c_init=c0)
+    L0 = s.ledger()
+    s.step(1)
+    assert s.events().tolist() == [[0, nx, oracle.EV_DISSOLVE]]
+    _, _, c, phi = s.fields()
+    assert s.classes()[0, 1, 0] == oracle.FLUID
+    assert c[0, 1, 0] == pytest.approx(c_ref[0, 2, 0], rel=1e-14)
+    Q = Vm * (c_ref[0, 2, 0] - c_ref[0, 1, 0]) - phi_ref[0, 1, 0]
+    for (y, x) in ((1, 1), (0, 0)):
+        assert phi_ref[0, y, x] - phi[0, y, x] == pytest.approx(Q / 2, rel=1e-12), (y, x)
+    assert _invariant(s.ledger()) == pytest.approx(_invariant(L0), rel=1e-13)
+    open_before = s.ledger()["open_in"]
+    s.step(5)
+    L = s.ledger()
+    assert L["open_in"] > open_before
+    assert _invariant(L) == pytest.approx(_invariant(L0), rel=1e-13)

@@ -157,23 +157,28 @@ def test_hand_evaluated_phase_change_events_match_oracle(case):
         assert lo["unpaid"] < 0.0
 
 
-@pytest.mark.parametrize("case", ["bulk_precipitations", "wall_precipitations", "dirichlet_neighbour",
+@pytest.mark.parametrize("case", ["corner_precipitations", "wall_precipitations", "dirichlet_neighbour",
                                   "inlet_face"])
 def test_hand_evaluated_events_near_other_boundaries_match_oracle(case):
     # the further configurations the oracle is pinned on by hand: two
-    # precipitations sharing a fluid neighbour (open fluid: equal split;
-    # flat wall: nothing sideways), a dissolution above a Dirichlet cell,
-    # and a dissolution on the inlet face
+    # precipitations sharing a fluid neighbour (concave corner: 5 : 1 split
+    # along the post-event normals; flat wall: nothing sideways), a
+    # dissolution above a Dirichlet cell, and a dissolution on the inlet face
     Vm = 0.4
     p = dict(dim=2, flow_q=0, solute_q=5, tau_solute=1.0, k_r=0.5, molar_volume=Vm, phase_change=1,
              precision="fp64", event_log_capacity=1024)
     init = {}
-    if case == "bulk_precipitations":
-        nx, ny = 7, 5
+    if case == "corner_precipitations":
+        # (the open-fluid pair of the oracle pin starts at phi = 1, which the
+        # C ABI rejects: on the GPU only cells next to reactive cells test the
+        # threshold, so a fluid cell must reach phi >= 1 through its shares)
+        nx = ny = 8
         mask = np.zeros((1, ny, nx), np.uint8)
-        phi0 = np.zeros((1, ny, nx))
-        phi0[0, 2, 2] = phi0[0, 2, 4] = 1.0
-        p.update(bc=("periodic",) * 3, c_eq=0.0, c_init=0.8)
+        mask[0, 0:2, :] = 1
+        mask[0, :, 0:2] = 1
+        phi0 = np.where(mask == 1, 1.0, 0.0)
+        phi0[0, 3, 2] = phi0[0, 2, 3] = 1.0 - 1e-12
+        p.update(bc=("periodic",) * 3, c_eq=0.0, c_init=1.0)
     elif case == "wall_precipitations":
         nx, ny = 5, 6
         mask = np.zeros((1, ny, nx), np.uint8)

@@ -415,3 +415,43 @@ def test_dissolution_at_the_inlet_face_by_hand():
     L = s.ledger()
     assert L["open_in"] > open_before
     assert _invariant(L) == pytest.approx(_invariant(L0), rel=1e-13)
+
+
+def test_corner_precipitations_split_by_post_event_normals_by_hand():
+    """Two bumps precipitate in the same step in a concave corner (walls at
+    x <= 1 and y <= 1), each next to one wall, diagonal to each other, with
+    the fluid cell (3, 3) as a shared neighbour (reading R5).  The normals are
+    taken on the post-event geometry, so each bump sees the other: at (2, 3)
+    the isotropic gradient of the solid indicator (D2Q9 weights times 36) is
+    4 (-1, 0) + (-1, -1) + (-1, 1) + (1, -1) = (-5, -1), n = (5, 1) / sqrt(26),
+    and the excess splits 5 : 1 between the links +x and +y (the link -y has
+    (e.n)+ = 0); by symmetry (3, 2) splits 5 : 1 between +y and +x.  The
+    shared cell receives 5/6 of each excess, the corner cell (2, 2) none."""
+    n, Vm = 8, 0.4
+    mask = np.zeros((1, n, n), np.uint8)
+    mask[0, 0:2, :] = 1
+    mask[0, :, 0:2] = 1
+    phi0 = np.where(mask == 1, 1.0, 0.0)
+    phi0[0, 3, 2] = phi0[0, 2, 3] = 1.0 - 1e-12
+    p = dict(dim=2, nx=n, ny=n, flow_q=0, solute_q=5, bc=("periodic",) * 3, tau_solute=1.0, k_r=0.5, c_eq=0.0,
+             c_init=1.0, molar_volume=Vm)
+    ref = oracle.OracleSim(dict(p, phase_change=0), mask, phi_init=phi0)
+    ref.step(1)
+    _, _, c_ref, phi_ref = ref.fields()
+    s = oracle.OracleSim(dict(p, phase_change=1), mask, phi_init=phi0)
+    L0 = s.ledger()
+    s.step(1)
+    assert s.events().tolist() == [[0, 3 + 2 * n, oracle.EV_PRECIPITATE], [0, 2 + 3 * n, oracle.EV_PRECIPITATE]]
+    nrm = s.normals()[0]
+    assert np.allclose(nrm[3, 2, :2], np.array([5.0, 1.0]) / np.sqrt(26.0), rtol=1e-15)
+    assert np.allclose(nrm[2, 3, :2], np.array([1.0, 5.0]) / np.sqrt(26.0), rtol=1e-15)
+    _, _, c, phi = s.fields()
+    eA = (phi_ref[0, 3, 2] + Vm * c_ref[0, 3, 2] - 1.0) / Vm
+    eB = (phi_ref[0, 2, 3] + Vm * c_ref[0, 2, 3] - 1.0) / Vm
+    assert eA > 0.0 and eB > 0.0
+    assert c[0, 3, 3] == pytest.approx(c_ref[0, 3, 3] + 5.0 / 6.0 * (eA + eB), rel=1e-13)
+    assert c[0, 4, 2] == pytest.approx(c_ref[0, 4, 2] + eA / 6.0, rel=1e-13)
+    assert c[0, 2, 4] == pytest.approx(c_ref[0, 2, 4] + eB / 6.0, rel=1e-13)
+    assert c[0, 2, 2] == pytest.approx(c_ref[0, 2, 2], rel=1e-14)
+    assert phi[0, 3, 2] == 1.0 and phi[0, 2, 3] == 1.0
+    assert _invariant(s.ledger()) == pytest.approx(_invariant(L0), rel=1e-13)

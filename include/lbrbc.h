@@ -69,6 +69,18 @@ enum { LBRBC_SCHEME_NEW = 0, LBRBC_SCHEME_VERHAEGHE = 1, LBRBC_SCHEME_PATEL_JU =
 
 enum { LBRBC_FP32 = 0, LBRBC_FP64 = 1 };
 
+/* Population storage (no counterpart in the paper; results are bitwise the
+ * same either way).  DENSE: every cell of the padded grid holds populations.
+ * SPARSE: only the stored cells do -- fluid cells, wet boundary cells and the
+ * solid cells next to those (the cells one dissolution can turn into
+ * boundary cells) -- numbered in row-major order in three ranges, with a
+ * neighbour table for streaming; in porous media a warp then moves whole
+ * population lines.  When a phase change needs a cell outside the stored set
+ * the layout is repacked on the device within that step.  AUTO picks SPARSE
+ * when under 85 % of the lanes of the dense grid's 32-cell row segments would
+ * hold fluid cells, else DENSE.  Batched domains always use DENSE. */
+enum { LBRBC_LAYOUT_AUTO = 0, LBRBC_LAYOUT_DENSE = 1, LBRBC_LAYOUT_SPARSE = 2 };
+
 /* Cell codes of the mask given to lbrbc_create. */
 enum { LBRBC_CELL_FLUID = 0, LBRBC_CELL_REACTIVE = 1, LBRBC_CELL_DIRICHLET = 2 };
 
@@ -100,6 +112,7 @@ typedef struct {
     double c_inlet;          /* inlet concentration (OPEN x)                        */
     double u_inlet;          /* plug inlet velocity when no inlet profile is given  */
     double rho_outlet;       /* outlet density (OPEN x)                             */
+    int layout;              /* LBRBC_LAYOUT_* (0: AUTO)                              */
 } lbrbc_params;
 
 /* Optional per-cell inputs; any pointer may be NULL.  All host pointers. */
@@ -225,6 +238,13 @@ lbrbc_status lbrbc_profile_step(lbrbc_sim *sim, int64_t n, void *stream, double 
 /* out[0] fluid cells, out[1] wet boundary cells at creation, out[2] kernel
  * launches per time step (host memory, 3 entries). */
 lbrbc_status lbrbc_info(lbrbc_sim *sim, int64_t *out);
+
+/* Population storage of the simulation (host memory, 4 entries): out[0]
+ * LBRBC_LAYOUT_DENSE or LBRBC_LAYOUT_SPARSE, out[1] cells holding
+ * populations (SPARSE: stored cells now; DENSE: padded grid slots), out[2]
+ * repackings of the SPARSE layout so far, out[3] bytes of population
+ * storage.  Synchronises the stream of the last lbrbc_step. */
+lbrbc_status lbrbc_layout_info(lbrbc_sim *sim, int64_t *out);
 
 /* ---- Batches of independent domains ------------------------------------
  * Many domains of uneven size and their own parameters (same lattices and

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(LIST_BLOCK) kb_bound(const DomainDesc<T>* __re
         const DomainDesc<T>& D = dd[ch.x];
         const int e = ch.y * LIST_BLOCK + threadIdx.x;
         DiffSum<T> racc, dacc;
-        if (e < *D.a.nb) bound_entry<T, LG, ODD>(D.a, D.p, D.q, e, racc, dacc);
+        if (e < *D.a.nb) bound_entry<T, D3Q19, LG, ODD, false>(D.a, D.p, D.q, e, racc, dacc);
         racc = warp_merge(racc);
         dacc = warp_merge(dacc);
         __syncthreads();
@@ -127,6 +127,7 @@ class BatchEngine final : public IBatch {
             auto* e = new Engine<T, LF, LG>();
             e->set_batched();
             e->force_list(true);
+            e->force_dense(true);
             doms_.emplace_back(e);
             const int rc = e->init(P[i], masks[i], inits ? &inits[i] : nullptr, err);
             if (rc) {

@@ -204,6 +204,30 @@ struct Dev {
     int* err;
     // compaction scratch
     int* blk;             // per chunk counts / offsets
+    // Active-cell ("sparse") population storage: populations only for the
+    // stored cells S (fluid, wet boundary and a margin of solid cells next to
+    // them), numbered in three row-major ranges (cells fluid at the last
+    // packing, boundary cells, margin) and blocked by 32 like the dense
+    // layout.  Null / 0 for the dense layout.
+    int sparse;
+    long long cap_s;      // capacity of the stored-cell arrays (multiple of 32)
+    int* ns;              // number of stored cells
+    int* cmap;            // NP: compact index of a padded cell, -1 if not stored
+    int* cid;             // cap_s: padded index of compact cell n
+    uint32_t* nwc;        // cap_s: node word of compact cell n
+    int* nbt;             // (QS - 1) * cap_s: compact index of n + e_s (stencil direction s), -1 if not stored
+    int* b_cn;            // cap_b: compact index of each wet boundary cell
+    int* rown;            // NP: owner of a cell of the event region (-1 outside), sparse event path
+    int* repack;          // [0] set when a cell needs storage it does not have
+    int* nrepack;         // repackings done
+    // repacking targets (phase change only): new numbering and populations
+    int* ns2;
+    int* cmap2;
+    int* cid2;
+    uint8_t* scode;       // NP: range of each cell in the stored set
+    int* stot;            // [3]: cells per range
+    T* F2;
+    T* G2;
 };
 
 template <class LG>
@@ -402,37 +426,102 @@ __device__ __forceinline__ void st_pop(T* p, T v) {
 #endif
 }
 
-// Where a fluid cell's pre-collision populations come from: GlobalSrc reads
-// the AA slot (read_slot) directly from HBM.
+// Node-word flags of fluid cells on the inlet (x = 0) and outlet (x = nx - 1)
+// faces of an open x axis.
+constexpr uint32_t NW_INLET = 1u << 30;
+constexpr uint32_t NW_OUTLET = 1u << 31;
+
+// Where a fluid cell's pre-collision populations come from and where its
+// post-collision ones go.  GlobalSrc: the dense AA layout (writes never
+// depend on the geometry).
 template <typename T, class LF, class LG, bool ODD>
 struct GlobalSrc {
+    static constexpr bool kTargets = false;  // writes do not depend on the neighbours' classes
     const T* __restrict__ F;
     const T* __restrict__ G;
     Blk<LF> kF;
     Blk<LG> kG;
+    T* Fw;
+    T* Gw;
     __device__ __forceinline__ T f(int i, bool inactive) const { return ld_pop(F + read_slot<LF, ODD>(kF, i, inactive)); }
     __device__ __forceinline__ T g(int i, bool inactive) const { return ld_pop(G + read_slot<LG, ODD>(kG, i, inactive)); }
+    __device__ __forceinline__ void fput(int i, T v, bool) const { st_pop(Fw + write_slot<LF, ODD>(kF, i), v); }
+    __device__ __forceinline__ void gput(int i, T v, bool) const { st_pop(Gw + write_slot<LG, ODD>(kG, i), v); }
 };
 
-// One fluid cell (x, y, z) of one step with node word w; shared by the
-// single-domain and batched sweeps.
+// Stencil of the neighbour table of the active-cell layout: the flow lattice
+// when there is one (its directions include the solute lattice's), else the
+// solute lattice.
+template <class LF, class LG>
+struct Stencil {
+    using L = LF;
+};
+template <class LG>
+struct Stencil<NoFlow, LG> {
+    using L = LG;
+};
+
+// Stencil direction with the velocity of direction j of lattice L.
+template <class LS, class L>
+__host__ __device__ constexpr int sdir(int j) {
+    for (int s = 0; s < LS::Q; ++s)
+        if (LS::cx(s) == L::cx(j) && LS::cy(s) == L::cy(j) && LS::cz(s) == L::cz(j)) return s;
+    return -1;
+}
+
+// Active-cell layout, own-slot convention.  Even step: a cell reads its own
+// slot i and writes f*_i into its own slot opp(i).  Odd step: it reads
+// f_i from slot opp(i) of the source x - e_i (its own slot i when the source
+// is inactive: the value there is its own f*_opp(i), halfway bounce-back) and
+// writes f*_i into slot i of x + e_i (its own slot opp(i) when that target
+// is inactive).  No population ever lives in an inactive cell, so the
+// storage holds the stored cells only; neighbours come from the table.
+template <typename T, class LF, class LG, bool ODD>
+struct SparseSrc {
+    static constexpr bool kTargets = true;  // writes go to an inactive target's own-slot fallback
+    using LS = typename Stencil<LF, LG>::L;
+    const T* __restrict__ F;
+    const T* __restrict__ G;
+    const int* __restrict__ nbt;
+    uint32_t n, cap;
+    T* Fw;
+    T* Gw;
+    __device__ __forceinline__ uint32_t nb(int s) const { return (uint32_t)__ldg(nbt + (size_t)(s - 1) * cap + n); }
+    template <class L>
+    __device__ __forceinline__ uint32_t rd(int i, bool inactive) const {
+        if (!ODD || inactive || i == 0) return pslot<L>(i, n);
+        return pslot<L>(L::opp(i), nb(sdir<LS, L>(L::opp(i))));
+    }
+    template <class L>
+    __device__ __forceinline__ uint32_t wr(int i, bool inactive) const {
+        if (!ODD || inactive || i == 0) return pslot<L>(L::opp(i), n);
+        return pslot<L>(i, nb(sdir<LS, L>(i)));
+    }
+    __device__ __forceinline__ T f(int i, bool inactive) const { return ld_pop(F + rd<LF>(i, inactive)); }
+    __device__ __forceinline__ T g(int i, bool inactive) const { return ld_pop(G + rd<LG>(i, inactive)); }
+    __device__ __forceinline__ void fput(int i, T v, bool inactive) const { st_pop(Fw + wr<LF>(i, inactive), v); }
+    __device__ __forceinline__ void gput(int i, T v, bool inactive) const { st_pop(Gw + wr<LG>(i, inactive), v); }
+};
+
+// One fluid cell of one step with node word w: stream (read side), open
+// boundaries, moments, collision, write.  id is the cell's padded index
+// (used for the adjoint tape), (y, z) its position (used on open x faces).
+// Shared by the dense, active-cell and batched sweeps.
 template <typename T, class LF, class LG, bool ODD, class Src>
-__device__ __forceinline__ void fluid_cell_src(const Dev<T>& a, const Phys& p, const PhysT<T>& q, int x, int y, int z,
-                                               uint32_t id, uint32_t w, const Nbr32& d, const Src& src) {
+__device__ __forceinline__ void fluid_cell_src(const Dev<T>& a, const Phys& p, const PhysT<T>& q, uint32_t id,
+                                               uint32_t w, const Src& src, bool inlet, bool outlet, int y, int z) {
     constexpr int QF = LF::Q, QG = LG::Q;
     const Geo& g = a.geo;
-    T* __restrict__ F = a.F;
-    T* __restrict__ G = a.G;
-    const bool inlet = g.open_x && x == 0;
-    const bool outlet = g.open_x && x == g.nx - 1;
-    const bool plain = (w >> FBIT) == 0u && !inlet && !outlet;
+    const bool plain = ((w & ~(NW_INLET | NW_OUTLET)) >> FBIT) == 0u && !inlet && !outlet;
 
     // Warps whose cells all read the plain slots take a path with no
     // per-direction tests; the others pick, per direction, the plain slot or
-    // the swapped one of an inactive source.
+    // the swapped one of an inactive source.  (All sources active means all
+    // targets active too: the sources of a cell are all its neighbours.)
+    const bool wplain = __all_sync(__activemask(), plain);
     T f[QF > 0 ? QF : 1];
     T gg[QG];
-    if (__all_sync(__activemask(), plain)) {
+    if (wplain) {
 #pragma unroll
         for (int i = 0; i < QF; ++i) f[i] = src.f(i, false);
 #pragma unroll
@@ -487,8 +576,13 @@ __device__ __forceinline__ void fluid_cell_src(const Dev<T>& a, const Phys& p, c
     T ux = T(0), uy = T(0), uz = T(0), rho = T(1);
     if constexpr (QF > 0) {
         flow_pairs<LF, T>(reinterpret_cast<T(&)[QF]>(f), rho, ux, uy, uz, p, q);
+        if (!Src::kTargets || wplain) {
 #pragma unroll
-        for (int i = 0; i < QF; ++i) st_pop(F + write_slot<LF, ODD>(src.kF, i), f[i]);
+            for (int i = 0; i < QF; ++i) src.fput(i, f[i], false);
+        } else {
+#pragma unroll
+            for (int i = 0; i < QF; ++i) src.fput(i, f[i], i > 0 && ((w >> (FBIT + LF::opp(i) - 1)) & 1u));
+        }
     }
     T C;
     solute_pairs<LG, T>(gg, C, ux, uy, uz, p, q);
@@ -498,8 +592,13 @@ __device__ __forceinline__ void fluid_cell_src(const Dev<T>& a, const Phys& p, c
         a.tape_u[3 * (size_t)id + 1] = (float)uy;
         a.tape_u[3 * (size_t)id + 2] = (float)uz;
     }
+    if (!Src::kTargets || wplain) {
 #pragma unroll
-    for (int i = 0; i < QG; ++i) st_pop(G + write_slot<LG, ODD>(src.kG, i), gg[i]);
+        for (int i = 0; i < QG; ++i) src.gput(i, gg[i], false);
+    } else {
+#pragma unroll
+        for (int i = 0; i < QG; ++i) src.gput(i, gg[i], i > 0 && ((w >> (GBIT + LG::opp(i) - 1)) & 1u));
+    }
     if (outlet) {
         const int face = y + g.ny * z;
         a.side[4 * face + 0] = (double)ux;
@@ -516,8 +615,10 @@ __device__ __forceinline__ void fluid_cell(const Dev<T>& a, const Phys& p, const
     const uint32_t w = a.nw[id];
     if ((w & 3u) != CLS_FLUID) return;
     const Nbr32 d = nbr32(g, x, y, z);
-    const GlobalSrc<T, LF, LG, ODD> src{a.F, a.G, blk_of<LF>(id, d), blk_of<LG>(id, d)};
-    fluid_cell_src<T, LF, LG, ODD>(a, p, q, x, y, z, id, w, d, src);
+    const GlobalSrc<T, LF, LG, ODD> src{a.F, a.G, blk_of<LF>(id, d), blk_of<LG>(id, d), a.F, a.G};
+    const bool inlet = g.open_x && x == 0;
+    const bool outlet = g.open_x && x == g.nx - 1;
+    fluid_cell_src<T, LF, LG, ODD>(a, p, q, id, w, src, inlet, outlet, y, z);
 }
 
 template <typename T, class LF, class LG, bool ODD>
@@ -525,6 +626,28 @@ __global__ void __launch_bounds__(FLUID_BLOCK, sizeof(T) == 4 ? 8 : 5) k_fluid(c
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= a.geo.nx) return;
     fluid_cell<T, LF, LG, ODD>(a, p, q, x, blockIdx.y, blockIdx.z);
+}
+
+// The fluid sweep of the active-cell layout: one thread per stored cell in
+// compact order (cells fluid at the last packing first, row-major), so a
+// warp's 32 cells read and write whole 128-byte population lines whatever
+// the geometry.
+template <typename T, class LF, class LG, bool ODD>
+__global__ void __launch_bounds__(FLUID_BLOCK, sizeof(T) == 4 ? 8 : 5) k_fluid_sp(const Dev<T> a, const Phys p, const PhysT<T> q) {
+    const int ns = *a.ns;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < ns; n += gridDim.x * blockDim.x) {
+        const uint32_t w = a.nwc[n];
+        if ((w & 3u) != CLS_FLUID) continue;
+        const bool inlet = (w & NW_INLET) != 0u, outlet = (w & NW_OUTLET) != 0u;
+        uint32_t id = 0;
+        int x = 0, y = 0, z = 0;
+        if (inlet || outlet || a.tape_u) {
+            id = (uint32_t)a.cid[n];
+            coords(a.geo, id, x, y, z);
+        }
+        const SparseSrc<T, LF, LG, ODD> src{a.F, a.G, a.nbt, (uint32_t)n, (uint32_t)a.cap_s, a.F, a.G};
+        fluid_cell_src<T, LF, LG, ODD>(a, p, q, id, w, src, inlet, outlet, y, z);
+    }
 }
 
 // The same sweep over the compacted fluid cells: every lane of a warp has a
@@ -656,25 +779,62 @@ __device__ __forceinline__ void unpack_xyz(uint64_t v, int& x, int& y, int& z) {
 
 // One wet boundary cell (list entry e) of one step; adds its reacted mass
 // (or Dirichlet inflow) to racc (dacc).
-template <typename T, class LG, bool ODD>
+// Solute slots of a wet boundary cell: dense AA layout (from the cell's
+// coordinates) or active-cell layout (from its compact index and the
+// neighbour table; LF only names the table's stencil).
+template <typename T, class LF, class LG, bool ODD, bool SP>
+struct BoundSlots {
+    Blk<LG> kb;
+    uint32_t n;
+    const int* nbt;
+    uint32_t cap;
+    __device__ __forceinline__ BoundSlots(const Dev<T>& a, int e) {
+        if constexpr (SP) {
+            n = (uint32_t)a.b_cn[e];
+            nbt = a.nbt;
+            cap = (uint32_t)a.cap_s;
+        } else {
+            int x, y, z;
+            unpack_xyz(a.b_xyz[e], x, y, z);
+            const uint32_t b = (uint32_t)a.geo.idx(x, y, z);
+            kb = blk_of<LG>(b, nbr32(a.geo, x, y, z));
+        }
+    }
+    __device__ __forceinline__ uint32_t rd(int i, bool inactive) const {
+        if constexpr (SP) {
+            using LS = typename Stencil<LF, LG>::L;
+            if (!ODD || inactive || i == 0) return pslot<LG>(i, n);
+            return pslot<LG>(LG::opp(i), (uint32_t)nbt[(size_t)(sdir<LS, LG>(LG::opp(i)) - 1) * cap + n]);
+        } else {
+            return read_slot<LG, ODD>(kb, i, inactive);
+        }
+    }
+    __device__ __forceinline__ uint32_t wr(int i, bool inactive) const {
+        if constexpr (SP) {
+            using LS = typename Stencil<LF, LG>::L;
+            if (!ODD || inactive || i == 0) return pslot<LG>(LG::opp(i), n);
+            return pslot<LG>(i, (uint32_t)nbt[(size_t)(sdir<LS, LG>(i) - 1) * cap + n]);
+        } else {
+            return write_slot<LG, ODD>(kb, i);
+        }
+    }
+};
+
+template <typename T, class LF, class LG, bool ODD, bool SP>
 __device__ __forceinline__ void bound_entry(const Dev<T>& a, const Phys& p, const PhysT<T>& q, int e, DiffSum<T>& racc,
                                             DiffSum<T>& dacc) {
     constexpr int Q = LG::Q;
-    const Geo& g = a.geo;
     T* __restrict__ G = a.G;
     const T cref = q.cref;
     const T gam = q.gamma, ics2 = q.ics2;
-    int x, y, z;
-    unpack_xyz(a.b_xyz[e], x, y, z);
-    const uint32_t b = (uint32_t)g.idx(x, y, z);
-    const Nbr32 d = nbr32(g, x, y, z);
-    const Blk<LG> kb = blk_of<LG>(b, d);
+    const BoundSlots<T, LF, LG, ODD, SP> kb(a, e);
+    const uint32_t b = (uint32_t)a.b_idx[e];
     const uint32_t bw = a.b_word[e];
     T gp[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const bool inactive = i > 0 && ((bw >> (i - 1)) & 1u);
-        gp[i] = G[read_slot<LG, ODD>(kb, i, inactive)];
+        gp[i] = G[kb.rd(i, inactive)];
     }
     T gq[Q];
 #pragma unroll
@@ -726,7 +886,7 @@ __device__ __forceinline__ void bound_entry(const Dev<T>& a, const Phys& p, cons
     if (!isfinite(C)) *a.err |= ERR_NUMERIC;
     collide_solute<LG, T>(gq, C, T(0), T(0), T(0), p, q);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) G[write_slot<LG, ODD>(kb, i)] = gq[i];
+    for (int i = 0; i < Q; ++i) G[kb.wr(i, i > 0 && ((bw >> (LG::opp(i) - 1)) & 1u))] = gq[i];
     const int sg = ms.sign();
     if (dir) {
         dacc.merge(ms);
@@ -748,12 +908,12 @@ __device__ __forceinline__ void bound_entry(const Dev<T>& a, const Phys& p, cons
     if (p.phase_change && dle0(ph)) push_event(a.nev, a.cap_e, a.ev_node, a.ev_kind, a.err, (int)b, EV_DISSOLVE);
 }
 
-template <typename T, class LG, bool ODD>
+template <typename T, class LF, class LG, bool ODD, bool SP>
 __global__ void __launch_bounds__(LIST_BLOCK, 4) k_bound(const Dev<T> a, const Phys p, const PhysT<T> q) {
     const int n = *a.nb;
     DiffSum<T> racc, dacc;  // reacted mass and Dirichlet inflow of this thread
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
-        bound_entry<T, LG, ODD>(a, p, q, e, racc, dacc);
+        bound_entry<T, LF, LG, ODD, SP>(a, p, q, e, racc, dacc);
     // each block owns its two accumulators (fixed grid): no atomics and a
     // fixed summation order
     __shared__ __align__(16) unsigned char red_raw[2 * (LIST_BLOCK / 32) * sizeof(DiffSum<T>)];
@@ -805,17 +965,28 @@ __global__ void __launch_bounds__(LIST_BLOCK) k_fend(const Dev<T> a, const Phys 
 // ---------------------------------------------------------------------------
 // Post-collision populations at their plain AA positions.
 // ---------------------------------------------------------------------------
-template <class L, typename T>
-__device__ __forceinline__ long long post_slot(long long id, const Nbr& d, int i, long long NP, bool lastodd) {
-    (void)NP;
-    return lastodd ? pslot64<L>(i, id + off<L>(d, i)) : pslot64<L>(L::opp(i), id);
+// Slot of the post-collision population f*_i of cell id in the current state
+// (lastodd: the last step was odd).  Dense layout: the AA position.  Active-
+// cell layout (own-slot convention): after an even step the cell's own slot
+// opp(i); after an odd step slot i of the neighbour id + e_i when that
+// neighbour is active for the lattice (flow: fluid; solute: not solid), else
+// the own slot opp(i).  FLOW: L is the flow lattice.
+template <class L, bool FLOW, typename T>
+__device__ __forceinline__ long long post_slot(const Dev<T>& a, long long id, const Nbr& d, int i, bool lastodd) {
+    if (!a.sparse) return lastodd ? pslot64<L>(i, id + off<L>(d, i)) : pslot64<L>(L::opp(i), id);
+    if (lastodd && i != 0) {
+        const long long nb = id + off<L>(d, i);
+        const uint32_t c = a.nw[nb] & 3u;
+        if (FLOW ? c == CLS_FLUID : c != CLS_SOLID) return pslot64<L>(i, a.cmap[nb]);
+    }
+    return pslot64<L>(L::opp(i), a.cmap[id]);
 }
 
-template <class L, typename T>
-__device__ __forceinline__ T post_sum(const T* A, long long id, const Nbr& d, long long NP, bool lastodd) {
+template <class L, bool FLOW, typename T>
+__device__ __forceinline__ T post_sum(const Dev<T>& a, const T* A, long long id, const Nbr& d, bool lastodd) {
     T s = T(0);
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) s += A[post_slot<L, T>(id, d, i, NP, lastodd)];
+    for (int i = 0; i < L::Q; ++i) s += A[post_slot<L, FLOW, T>(a, id, d, i, lastodd)];
     return s;
 }
 
@@ -928,7 +1099,7 @@ __global__ void k_ev_compute(const Dev<T> a, const Phys p, int lastodd) {
         int x, y, z;
         coords(g, id, x, y, z);
         const Nbr d = nbr_deltas(g, x, y, z);
-        const double Cself = p.cref + (double)post_sum<LG, T>(a.G, id, d, NP, lastodd);
+        const double Cself = p.cref + (double)post_sum<LG, false, T>(a, a.G, id, d, lastodd);
         if (a.ev_kind[e] == EV_DISSOLVE) {
             double sc = 0.0, sr = 0.0;
             int nfl = 0, ns = 0;
@@ -939,8 +1110,8 @@ __global__ void k_ev_compute(const Dev<T> a, const Phys p, int lastodd) {
                 const long long nb = g.idx(xx, yy, zz);
                 if ((a.nw[nb] & 3u) == CLS_FLUID) {
                     const Nbr dn = nbr_deltas(g, xx, yy, zz);
-                    sc += p.cref + (double)post_sum<LG, T>(a.G, nb, dn, NP, lastodd);
-                    if constexpr (LF::Q > 0) sr += 1.0 + (double)post_sum<LF, T>(a.F, nb, dn, NP, lastodd);
+                    sc += p.cref + (double)post_sum<LG, false, T>(a, a.G, nb, dn, lastodd);
+                    if constexpr (LF::Q > 0) sr += 1.0 + (double)post_sum<LF, true, T>(a, a.F, nb, dn, lastodd);
                     else sr += 1.0;
                     nfl++;
                 }
@@ -1000,16 +1171,16 @@ __global__ void k_ev_apply_self(const Dev<T> a, const Phys p, int lastodd) {
             const double cinit = a.ev_val[e], rinit = a.ev_val[a.cap_e + e];
 #pragma unroll
             for (int i = 0; i < LG::Q; ++i)
-                a.G[post_slot<LG, T>(id, d, i, NP, lastodd)] = T(gweight<LG>(p, i) * (cinit - p.cref));
+                a.G[post_slot<LG, false, T>(a, id, d, i, lastodd)] = T(gweight<LG>(p, i) * (cinit - p.cref));
             if constexpr (LF::Q > 0) {
 #pragma unroll
-                for (int i = 0; i < LF::Q; ++i) a.F[post_slot<LF, T>(id, d, i, NP, lastodd)] = T(LF::w(i) * (rinit - 1.0));
+                for (int i = 0; i < LF::Q; ++i) a.F[post_slot<LF, true, T>(a, id, d, i, lastodd)] = T(LF::w(i) * (rinit - 1.0));
             }
             a.phi[id] = 0.0;
         } else {
 #pragma unroll
             for (int i = 0; i < LG::Q; ++i)
-                a.G[post_slot<LG, T>(id, d, i, NP, lastodd)] = T(-gweight<LG>(p, i) * p.cref);
+                a.G[post_slot<LG, false, T>(a, id, d, i, lastodd)] = T(-gweight<LG>(p, i) * p.cref);
             a.phi[id] = a.ev_val[e];
         }
     }
@@ -1060,7 +1231,7 @@ __global__ void k_ev_neighbours(const Dev<T> a, const Phys p, int lastodd) {
         if (dC != 0.0) {
             const Nbr d = nbr_deltas(g, x, y, z);
             for (int i = 0; i < LG::Q; ++i) {
-                const long long s = post_slot<LG, T>(tgt, d, i, NP, lastodd);
+                const long long s = post_slot<LG, false, T>(a, tgt, d, i, lastodd);
                 a.G[s] = T((double)a.G[s] + gweight<LG>(p, i) * dC);
             }
         }
@@ -1087,14 +1258,21 @@ __global__ void k_reclassify(const Dev<T> a, const Phys p, int lastodd, int forc
         if (!force && old != cls && a.evidx[id] < 0) {
             const Nbr d = nbr_deltas(g, x, y, z);
             if (old == CLS_BOUND && cls == CLS_SOLID) {
-                const double C = p.cref + (double)post_sum<LG, T>(a.G, id, d, NP, lastodd);
+                const double C = p.cref + (double)post_sum<LG, false, T>(a, a.G, id, d, lastodd);
                 if (a.kind[id] == KIND_REACTIVE) a.phi[id] += p.Vm * C;
                 else atomicAdd(&a.acc[1], -C);
             }
             if (cls != CLS_FLUID) {
+                if (a.sparse && a.cmap[id] < 0) {
+                    // a solid cell outside the stored set gained a fluid
+                    // neighbour: the layout is repacked before the next step,
+                    // and the repacking gives it its starting populations
+                    *a.repack = 1;
+                } else {
 #pragma unroll
-                for (int i = 0; i < LG::Q; ++i)
-                    a.G[post_slot<LG, T>(id, d, i, NP, lastodd)] = T(-gweight<LG>(p, i) * p.cref);
+                    for (int i = 0; i < LG::Q; ++i)
+                        a.G[post_slot<LG, false, T>(a, id, d, i, lastodd)] = T(-gweight<LG>(p, i) * p.cref);
+                }
             }
         }
         uint32_t w = cls;
@@ -1111,8 +1289,14 @@ __global__ void k_reclassify(const Dev<T> a, const Phys p, int lastodd, int forc
                 int xx = x - LG::cx(i), yy = y - LG::cy(i), zz = z - LG::cz(i);
                 if (class_at<LG>(g, a.kind, xx, yy, zz) == CLS_SOLID) w |= 1u << (GBIT + i - 1);
             }
+            if (g.open_x && x == 0) w |= NW_INLET;
+            if (g.open_x && x == g.nx - 1) w |= NW_OUTLET;
         }
         a.nw[id] = w;
+        if (a.sparse) {
+            const int c = a.cmap[id];
+            if (c >= 0) a.nwc[c] = w;
+        }
     }
 }
 
@@ -1240,6 +1424,7 @@ __global__ void k_write_lists(const Dev<T> a, const Phys p, int which, int force
         if (sel) {
             if (which == 0 && pos < a.cap_b) {
                 a.b_idx[pos] = (int)id;
+                if (a.sparse) a.b_cn[pos] = a.cmap[id];
                 a.b_xyz[pos] = pack_xyz(x, y, z);
                 a.bmap[id] = pos;
                 uint32_t bw = 0;
@@ -1286,6 +1471,317 @@ __global__ void k_write_lists(const Dev<T> a, const Phys p, int which, int force
     }
 }
 
+// ---------------------------------------------------------------------------
+// Active-cell layout: the stored set, its numbering and neighbour table, and
+// the event path's link swaps.
+// ---------------------------------------------------------------------------
+constexpr int RNONE = 0x7f7f7f7f;  // rown of a cell outside the event region (byte-filled)
+
+// Range of every in-grid cell in the stored set from the current classes:
+// 0 fluid, 1 wet boundary, 2 solid with a wet-boundary neighbour along the
+// solute lattice (the margin a dissolution can turn into boundary cells),
+// 3 not stored.
+template <typename T, class LG>
+__global__ void k_sp_mark(const Dev<T> a, uint8_t* __restrict__ code, const int* __restrict__ go) {
+    if (go && *go == 0) return;
+    const Geo& g = a.geo;
+    const long long total = (long long)g.nx * g.ny * g.nz;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(t % g.nx);
+        const int y = (int)((t / g.nx) % g.ny);
+        const int z = (int)(t / ((long long)g.nx * g.ny));
+        const long long id = g.idx(x, y, z);
+        const uint32_t c = a.nw[id] & 3u;
+        uint8_t r = c == CLS_FLUID ? 0 : (c == CLS_BOUND ? 1 : 3);
+        if (r == 3) {
+#pragma unroll
+            for (int o = 1; o < LG::Q; ++o) {
+                int xx = x + LG::cx(o), yy = y + LG::cy(o), zz = z + LG::cz(o);
+                if (wrap_inside(g, xx, yy, zz) && (a.nw[g.idx(xx, yy, zz)] & 3u) == CLS_BOUND) r = 2;
+            }
+        }
+        code[id] = r;
+    }
+}
+
+// Per chunk of SCAN_CHUNK cells (x-fastest order): cells of range r.
+template <typename T>
+__global__ void k_sp_count(const Dev<T> a, const uint8_t* __restrict__ code, int r, const int* __restrict__ go) {
+    if (go && *go == 0) return;
+    const Geo& g = a.geo;
+    const long long total = (long long)g.nx * g.ny * g.nz;
+    const long long chunk = blockIdx.x;
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    int local = 0;
+    for (long long t = chunk * SCAN_CHUNK + threadIdx.x; t < min(total, (chunk + 1) * SCAN_CHUNK); t += blockDim.x) {
+        const int x = (int)(t % g.nx);
+        const int y = (int)((t / g.nx) % g.ny);
+        const int z = (int)(t / ((long long)g.nx * g.ny));
+        local += code[g.idx(x, y, z)] == r;
+    }
+    atomicAdd(&cnt, local);
+    __syncthreads();
+    if (threadIdx.x == 0) a.blk[chunk] = cnt;
+}
+
+// Exclusive scan of the chunk counts (one block); the range total goes to
+// tot[r].
+template <typename T>
+__global__ void k_sp_scan(const Dev<T> a, int nchunks, int r, int* __restrict__ tot, const int* __restrict__ go) {
+    if (go && *go == 0) return;
+    __shared__ int part[1024];
+    const int per = (nchunks + blockDim.x - 1) / blockDim.x;
+    const int lo = threadIdx.x * per, hi = min(nchunks, lo + per);
+    int s = 0;
+    for (int c = lo; c < hi; ++c) s += a.blk[c];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int k = 0; k < (int)blockDim.x; ++k) {
+            const int v = part[k];
+            part[k] = run;
+            run += v;
+        }
+        tot[r] = run;
+    }
+    __syncthreads();
+    int run = part[threadIdx.x];
+    for (int c = lo; c < hi; ++c) {
+        const int v = a.blk[c];
+        a.blk[c] = run;
+        run += v;
+    }
+}
+
+// Compact indices of range r in chunk order after the ranges before it
+// (cmap_out must hold -1 for every cell beforehand).  Positions beyond the
+// capacity raise ERR_OVERFLOW and are not written.
+template <typename T>
+__global__ void k_sp_write(const Dev<T> a, const uint8_t* __restrict__ code, int r, const int* __restrict__ tot,
+                           int* __restrict__ cmap_out, int* __restrict__ cid_out, const int* __restrict__ go) {
+    if (go && *go == 0) return;
+    const Geo& g = a.geo;
+    const long long total = (long long)g.nx * g.ny * g.nz;
+    const long long chunk = blockIdx.x;
+    __shared__ int warp_tot[32];
+    __shared__ int base_s;
+    if (threadIdx.x == 0) {
+        int b = a.blk[chunk];
+        for (int k = 0; k < r; ++k) b += tot[k];
+        base_s = b;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw_ = blockDim.x >> 5;
+    const long long end = min(total, (chunk + 1) * SCAN_CHUNK);
+    for (long long t0 = chunk * SCAN_CHUNK; t0 < end; t0 += blockDim.x) {
+        const long long t = t0 + threadIdx.x;
+        bool sel = false;
+        long long id = 0;
+        if (t < end) {
+            const int x = (int)(t % g.nx);
+            const int y = (int)((t / g.nx) % g.ny);
+            const int z = (int)(t / ((long long)g.nx * g.ny));
+            id = g.idx(x, y, z);
+            sel = code[id] == r;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, sel);
+        if (lane == 0) warp_tot[wid] = __popc(bal);
+        __syncthreads();
+        int woff = 0, tt = 0;
+        for (int k = 0; k < nw_; ++k) {
+            if (k < wid) woff += warp_tot[k];
+            tt += warp_tot[k];
+        }
+        const int pos = base_s + woff + __popc(bal & ((1u << lane) - 1u));
+        if (sel) {
+            if (pos < a.cap_s) {
+                cmap_out[id] = pos;
+                cid_out[pos] = (int)id;
+            } else {
+                atomicOr(a.err, ERR_OVERFLOW);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) base_s += tt;
+        __syncthreads();
+    }
+}
+
+// Stored-cell count from the range totals.
+template <typename T>
+__global__ void k_sp_total(const Dev<T> a, const int* __restrict__ tot, int* __restrict__ ns_out,
+                           const int* __restrict__ go) {
+    if (go && *go == 0) return;
+    const long long n = (long long)tot[0] + tot[1] + tot[2];
+    *ns_out = (int)min(n, a.cap_s);
+}
+
+// Node words and neighbour table of the stored cells: nbt[s][n] is the
+// compact index of n + e_s (periodic wrap; -1 beyond a wall or open face or
+// when that cell is not stored).
+template <typename T, class LF, class LG>
+__global__ void k_sp_tables(const Dev<T> a, const int* __restrict__ go) {
+    if (go && *go == 0) return;
+    using LS = typename Stencil<LF, LG>::L;
+    const int ns = *a.ns;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < ns; n += (long long)gridDim.x * blockDim.x) {
+        const long long id = a.cid[n];
+        a.nwc[n] = a.nw[id];
+        const Nbr d = nbr_of(a.geo, id);
+#pragma unroll
+        for (int s = 1; s < LS::Q; ++s) a.nbt[(size_t)(s - 1) * a.cap_s + n] = a.cmap[id + off<LS>(d, s)];
+    }
+}
+
+// Event region of a step: the event cells and their neighbours along the
+// solute lattice.  A cell's owner is the smallest (event, direction) item
+// that reaches it.
+template <typename T, class LG>
+__global__ void k_sp_rmark(const Dev<T> a) {
+    const int n = min(*a.nev, a.cap_e);
+    const Geo& g = a.geo;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)n * LG::Q;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int e = (int)(t / LG::Q), o = (int)(t % LG::Q);
+        int x, y, z;
+        coords(g, a.ev_node[e], x, y, z);
+        x += LG::cx(o);
+        y += LG::cy(o);
+        z += LG::cz(o);
+        if (!wrap_inside(g, x, y, z)) continue;
+        atomicMin(&a.rown[g.idx(x, y, z)], (int)t);
+    }
+}
+
+// Swap the two slots of every link with an end in the event region whose
+// two ends are both active for the lattice under the classes in the node
+// words: after an odd step this turns the region into the even-step form
+// (each cell's f*_i in its own slot opp(i)), and back after the classes
+// change.  Each link is handled once: by its end in the region, or by the
+// end whose direction lies in the first half when both are.
+template <typename T, class L, bool FLOW>
+__device__ __forceinline__ void swap_links(const Dev<T>& a, T* A, long long c, const Nbr& d) {
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) {
+        const long long nb = c + off<L>(d, i);
+        if (i > L::H && a.rown[nb] != RNONE) continue;
+        const uint32_t cc = a.nw[c] & 3u, cn = a.nw[nb] & 3u;
+        const bool act = FLOW ? (cc == CLS_FLUID && cn == CLS_FLUID) : (cc != CLS_SOLID && cn != CLS_SOLID);
+        if (!act) continue;
+        const long long s1 = pslot64<L>(i, a.cmap[nb]), s2 = pslot64<L>(L::opp(i), a.cmap[c]);
+        const T v = A[s1];
+        A[s1] = A[s2];
+        A[s2] = v;
+    }
+}
+
+template <typename T, class LF, class LG>
+__global__ void k_sp_swap(const Dev<T> a) {
+    const int n = min(*a.nev, a.cap_e);
+    const Geo& g = a.geo;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)n * LG::Q;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int e = (int)(t / LG::Q), o = (int)(t % LG::Q);
+        int x, y, z;
+        coords(g, a.ev_node[e], x, y, z);
+        x += LG::cx(o);
+        y += LG::cy(o);
+        z += LG::cz(o);
+        if (!wrap_inside(g, x, y, z)) continue;
+        const long long c = g.idx(x, y, z);
+        if (a.rown[c] != (int)t) continue;
+        const Nbr d = nbr_deltas(g, x, y, z);
+        if constexpr (LF::Q > 0) swap_links<T, LF, true>(a, a.F, c, d);
+        swap_links<T, LG, false>(a, a.G, c, d);
+    }
+}
+
+template <typename T, class LG>
+__global__ void k_sp_rreset(const Dev<T> a) {
+    const int n = min(*a.nev, a.cap_e);
+    const Geo& g = a.geo;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)n * LG::Q;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int e = (int)(t / LG::Q), o = (int)(t % LG::Q);
+        int x, y, z;
+        coords(g, a.ev_node[e], x, y, z);
+        x += LG::cx(o);
+        y += LG::cy(o);
+        z += LG::cz(o);
+        if (!wrap_inside(g, x, y, z)) continue;
+        a.rown[g.idx(x, y, z)] = RNONE;
+    }
+}
+
+// Repacking (when a cell outside the stored set must be stored): the new
+// numbering is written to cmap2 / cid2 / ns2 by the k_sp_* kernels above,
+// then the populations move cell by cell into F2 / G2 (new cells start with
+// C = 0 and flow at rest) and everything is copied back.  Every kernel
+// returns at once unless a repacking is pending.
+template <typename T, class LF, class LG>
+__global__ void k_sp_gather(const Dev<T> a, const Phys p) {
+    if (*a.repack == 0) return;
+    constexpr int QF = LF::Q, QG = LG::Q;
+    const int ns2 = *a.ns2;
+    for (long long n2 = blockIdx.x * (long long)blockDim.x + threadIdx.x; n2 < ns2;
+         n2 += (long long)gridDim.x * blockDim.x) {
+        const int n = a.cmap[a.cid2[n2]];
+        if constexpr (QF > 0) {
+#pragma unroll
+            for (int i = 0; i < QF; ++i) a.F2[pslot64<LF>(i, n2)] = n >= 0 ? a.F[pslot64<LF>(i, n)] : T(0);
+        }
+#pragma unroll
+        for (int i = 0; i < QG; ++i)
+            a.G2[pslot64<LG>(i, n2)] = n >= 0 ? a.G[pslot64<LG>(i, n)] : T(-gweight<LG>(p, i) * p.cref);
+    }
+}
+
+template <typename T, class LF, class LG>
+__global__ void k_sp_commit(const Dev<T> a) {
+    if (*a.repack == 0) return;
+    constexpr int QF = LF::Q, QG = LG::Q;
+    const int ns2 = *a.ns2;
+    const long long NP = a.geo.NP;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (long long k = t0; k < (long long)QF * ns2; k += stride) {
+        const long long n = k % ns2, i = k / ns2;
+        a.F[pslot64<LF>((int)i, n)] = a.F2[pslot64<LF>((int)i, n)];
+    }
+    for (long long k = t0; k < (long long)QG * ns2; k += stride) {
+        const long long n = k % ns2, i = k / ns2;
+        a.G[pslot64<LG>((int)i, n)] = a.G2[pslot64<LG>((int)i, n)];
+    }
+    for (long long k = t0; k < ns2; k += stride) a.cid[k] = a.cid2[k];
+    for (long long k = t0; k < NP; k += stride) a.cmap[k] = a.cmap2[k];
+}
+
+template <typename T>
+__global__ void k_sp_commit_end(const Dev<T> a) {
+    if (*a.repack == 0) return;
+    *a.ns = *a.ns2;
+}
+
+template <typename T>
+__global__ void k_sp_repack_done(const Dev<T> a) {
+    if (*a.repack == 0) return;
+    *a.repack = 0;
+    *a.nrepack += 1;
+}
+
+// -1 everywhere (cmap2 before a repacking), when one is pending.
+template <typename T>
+__global__ void k_sp_clear2(const Dev<T> a) {
+    if (*a.repack == 0) return;
+    const long long NP = a.geo.NP;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < NP; k += (long long)gridDim.x * blockDim.x)
+        a.cmap2[k] = -1;
+}
+
 template <typename T>
 __global__ void k_ev_reset(const Dev<T> a) {
     const int n = min(*a.nev, a.cap_e);
@@ -1326,7 +1822,7 @@ __global__ void k_init(const Dev<T> a, const Phys p, const double* __restrict__ 
                 for (int i = 0; i < LF::Q; ++i) {
                     const double eu = LF::cx(i) * ux + LF::cy(i) * uy + LF::cz(i) * uz;
                     const double feq = LF::w(i) * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
-                    a.F[pslot64<LF>(i, id + off<LF>(d, i))] = T(feq - LF::w(i));
+                    a.F[post_slot<LF, true, T>(a, id, d, i, true)] = T(feq - LF::w(i));
                 }
             }
         }
@@ -1336,7 +1832,7 @@ __global__ void k_init(const Dev<T> a, const Phys p, const double* __restrict__ 
             for (int i = 0; i < LG::Q; ++i) {
                 const double eu = LG::cx(i) * ux + LG::cy(i) * uy + LG::cz(i) * uz;
                 const double w = gweight<LG>(p, i);
-                a.G[pslot64<LG>(i, id + off<LG>(d, i))] = T(C * w * (1.0 + eu * ics2) - w * p.cref);
+                a.G[post_slot<LG, false, T>(a, id, d, i, true)] = T(C * w * (1.0 + eu * ics2) - w * p.cref);
             }
         }
         if (g.open_x && x == g.nx - 1) {
@@ -1369,7 +1865,7 @@ __global__ void k_fields(const Dev<T> a, const Phys p, int lastodd, double* u, d
                 double s = 0.0;
 #pragma unroll
                 for (int i = 0; i < LF::Q; ++i) {
-                    const double v = (double)a.F[post_slot<LF, T>(id, d, i, NP, lastodd)];
+                    const double v = (double)a.F[post_slot<LF, true, T>(a, id, d, i, lastodd)];
                     s += v;
                     jx += LF::cx(i) * v;
                     jy += LF::cy(i) * v;
@@ -1381,7 +1877,7 @@ __global__ void k_fields(const Dev<T> a, const Phys p, int lastodd, double* u, d
                 jz /= r;
             }
         }
-        if (cls != CLS_SOLID) C = p.cref + (double)post_sum<LG, T>(a.G, id, d, NP, lastodd);
+        if (cls != CLS_SOLID) C = p.cref + (double)post_sum<LG, false, T>(a, a.G, id, d, lastodd);
         if (u) {
             u[3 * t] = jx;
             u[3 * t + 1] = jy;
@@ -1425,7 +1921,7 @@ __global__ void __launch_bounds__(RED_BLOCK) k_reduce_partial(const Dev<T> a, co
             const Nbr d = nbr_deltas(g, x, y, z);
             double s = 0.0;
 #pragma unroll
-            for (int i = 0; i < LG::Q; ++i) s += (double)a.G[post_slot<LG, T>(id, d, i, NP, lastodd)];
+            for (int i = 0; i < LG::Q; ++i) s += (double)a.G[post_slot<LG, false, T>(a, id, d, i, lastodd)];
             sc += p.cref + s;
         }
         sp += a.phi[id];

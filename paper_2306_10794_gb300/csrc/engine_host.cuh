@@ -155,6 +155,13 @@ class Engine final : public ISim {
             if (force_list_) want = SWEEP_LIST;
             // (the list sweep is not combined with phase change)
             if (want == SWEEP_LIST && !(fits && !P.phase_change)) want = SWEEP_DENSE;
+            // population layout: the active-cell layout in porous media
+            // (batched domains keep the dense layout)
+            int lay = P.layout;
+            if (force_dense_) lay = LBRBC_LAYOUT_DENSE;
+            if (lay == LBRBC_LAYOUT_AUTO) lay = lane_eff_ < 0.85 ? LBRBC_LAYOUT_SPARSE : LBRBC_LAYOUT_DENSE;
+            d_.sparse = lay == LBRBC_LAYOUT_SPARSE;
+            if (d_.sparse) want = SWEEP_DENSE;
             sweep_ = want;
             d_.use_fl = want == SWEEP_LIST;
             d_.cap_fl = (int)std::min<long long>(ncell_, std::max<long long>(2 * nfluid, nfluid + ncell_ / 8) + 1024);
@@ -164,9 +171,30 @@ class Engine final : public ISim {
 
         // device allocations
         constexpr int QF = LF::Q > 0 ? LF::Q : 0, QG = LG::Q;
-        if (QF) LB_CUDA(dalloc(&d_.F, (size_t)QF * NP));
-        else d_.F = nullptr;
-        LB_CUDA(dalloc(&d_.G, (size_t)QG * NP));
+        d_.F = d_.G = nullptr;
+        if (!d_.sparse) {
+            if (QF) LB_CUDA(dalloc(&d_.F, (size_t)QF * NP));
+            LB_CUDA(dalloc(&d_.G, (size_t)QG * NP));
+            popn_ = NP;
+        } else {
+            LB_CUDA(dalloc(&d_.cmap, (size_t)NP));
+            LB_CUDA(cudaMemset(d_.cmap, 0xff, NP * sizeof(int)));
+            LB_CUDA(dalloc(&d_.ns, 1));
+            LB_CUDA(dalloc(&d_.repack, 1));
+            LB_CUDA(dalloc(&d_.nrepack, 1));
+            LB_CUDA(cudaMemset(d_.ns, 0, sizeof(int)));
+            LB_CUDA(cudaMemset(d_.repack, 0, sizeof(int)));
+            LB_CUDA(cudaMemset(d_.nrepack, 0, sizeof(int)));
+            LB_CUDA(dalloc(&d_.scode, (size_t)NP));
+            LB_CUDA(cudaMemset(d_.scode, 3, NP));
+            LB_CUDA(dalloc(&d_.stot, 4));
+            if (P.phase_change) {
+                LB_CUDA(dalloc(&d_.rown, (size_t)NP));
+                LB_CUDA(cudaMemset(d_.rown, 0x7f, NP * sizeof(int)));
+                LB_CUDA(dalloc(&d_.ns2, 1));
+                LB_CUDA(dalloc(&d_.cmap2, (size_t)NP));
+            }
+        }
         LB_CUDA(dalloc(&d_.nw, (size_t)NP));
         LB_CUDA(dalloc(&d_.kind, (size_t)NP));
         LB_CUDA(dalloc(&d_.phi, (size_t)NP));
@@ -178,6 +206,7 @@ class Engine final : public ISim {
         LB_CUDA(dalloc(&d_.b_xyz, (size_t)d_.cap_b));
         LB_CUDA(dalloc(&d_.b_kappa, (size_t)(QG - 1) * d_.cap_b));
         LB_CUDA(dalloc(&d_.b_fslot, (size_t)(QG - 1) * d_.cap_b));
+        if (d_.sparse) LB_CUDA(dalloc(&d_.b_cn, (size_t)d_.cap_b));
         LB_CUDA(dalloc(&d_.bmap, (size_t)NP));
         LB_CUDA(dalloc(&d_.nf, 1));
         LB_CUDA(dalloc(&d_.f_idx, (size_t)d_.cap_f));
@@ -269,15 +298,24 @@ class Engine final : public ISim {
         LB_CUDA(cudaMemset(d_.acc, 0, 4 * sizeof(double)));
         LB_CUDA(cudaMemset(d_.err, 0, sizeof(int)));
         LB_CUDA(cudaMemset(d_.side, 0, 4 * sizeof(double) * g.ny * g.nz));
-        if (QF) LB_CUDA(cudaMemset(d_.F, 0, (size_t)QF * NP * sizeof(T)));
-        LB_CUDA(cudaMemset(d_.G, 0, (size_t)QG * NP * sizeof(T)));
+        if (!d_.sparse) {
+            if (QF) LB_CUDA(cudaMemset(d_.F, 0, (size_t)QF * NP * sizeof(T)));
+            LB_CUDA(cudaMemset(d_.G, 0, (size_t)QG * NP * sizeof(T)));
+        }
         // ghost cells are solid for every lattice
         {
             std::vector<uint32_t> nwh(NP, CLS_SOLID);
             LB_CUDA(cudaMemcpy(d_.nw, nwh.data(), NP * sizeof(uint32_t), cudaMemcpyHostToDevice));
         }
-        // classes, lists, initial populations
-        if (rebuild(own_, 0, 1, err)) return 2;
+        // classes, stored set (active-cell layout), lists, initial populations
+        if (!d_.sparse) {
+            if (rebuild(own_, 0, 1, err)) return 2;
+        } else {
+            enqueue_reclassify(own_, 0, 1);
+            if (build_stored(err)) return 2;
+            enqueue_lists(own_, 1);
+            LB_CUDA(cudaGetLastError());
+        }
         double *dc0 = nullptr, *du0 = nullptr;
         LB_CUDA(talloc(&dc0, (size_t)ncell_));
         LB_CUDA(cudaMemcpy(dc0, c0.data(), ncell_ * sizeof(double), cudaMemcpyHostToDevice));
@@ -465,6 +503,7 @@ class Engine final : public ISim {
     int host_nf() const { return (int)nf0_; }
     void set_batched() { batched_ = true; }
     void force_list(bool v) { force_list_ = v; }
+    void force_dense(bool v) { force_dense_ = v; }
     bool uses_list() const { return d_.use_fl != 0; }
     double lane_efficiency() const { return lane_eff_; }
     int host_nfl() const { return (int)nfluid_; }
@@ -504,7 +543,8 @@ class Engine final : public ISim {
         constexpr int QF = LF::Q > 0 ? LF::Q : 0, QG = LG::Q;
         const int64_t S = std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)n)));
         const int64_t nseg = (n + S - 1) / S;
-        const size_t fbytes = (size_t)QF * NP * sizeof(T), gbytes = (size_t)QG * NP * sizeof(T);
+        const size_t fbytes = (size_t)QF * popn_ * sizeof(T), gbytes = (size_t)QG * popn_ * sizeof(T);
+        const size_t lbytes = (size_t)QG * NP * sizeof(T);  // adjoint arrays: plain layout over the padded grid
         const size_t sbytes = (size_t)4 * d_.geo.ny * d_.geo.nz * sizeof(double);
         std::vector<void*> tmp;
         auto get = [&](size_t bytes, void** p) -> cudaError_t {
@@ -533,8 +573,8 @@ class Engine final : public ISim {
         const size_t hbytes = (size_t)(QG - 1) * d_.cap_b * sizeof(T);
         LB_ACUDA(get(hbytes * (size_t)(S + 1), &gtape));
         LB_ACUDA(get((size_t)3 * NP * sizeof(float) * (size_t)(S + 1), &utape));
-        LB_ACUDA(get(gbytes, &lam));
-        LB_ACUDA(get(gbytes, &nu));
+        LB_ACUDA(get(lbytes, &lam));
+        LB_ACUDA(get(lbytes, &nu));
         LB_ACUDA(get((size_t)NP * sizeof(double), &dkf));
         LB_ACUDA(get((size_t)2 * nbk * sizeof(double), &part));
         LB_ACUDA(get((size_t)NP * sizeof(double), &save_phi));
@@ -583,7 +623,7 @@ class Engine final : public ISim {
         LB_ACUDA(cudaMemcpyAsync(save_bacc, d_.bacc, 2 * nbacc_ * sizeof(double), cudaMemcpyDeviceToDevice, st));
         LB_ACUDA(cudaMemcpyAsync(save_acc, d_.acc, 4 * sizeof(double), cudaMemcpyDeviceToDevice, st));
         // reverse sweep
-        LB_ACUDA(cudaMemsetAsync(lam, 0, gbytes, st));
+        LB_ACUDA(cudaMemsetAsync(lam, 0, lbytes, st));
         LB_ACUDA(cudaMemsetAsync(dkf, 0, NP * sizeof(double), st));
         LB_ACUDA(cudaMemsetAsync(part, 0, 2 * nbk * sizeof(double), st));
         const dim3 g3((d_.geo.nx + FLUID_BLOCK - 1) / FLUID_BLOCK, d_.geo.ny, d_.geo.nz);
@@ -729,14 +769,94 @@ class Engine final : public ISim {
 
     // Reclassification and list rebuild (force = 1 at creation: unconditional).
     int rebuild(cudaStream_t st, int lastodd, int force, std::string& err) {
-        k_reclassify<T, LF, LG><<<grid_for(ncell_, 256), 256, 0, st>>>(d_, ph_, lastodd, force);
+        enqueue_reclassify(st, lastodd, force);
+        enqueue_lists(st, force);
+        LB_CUDA(cudaGetLastError());
+        return 0;
+    }
+
+    void enqueue_reclassify(cudaStream_t st, int form, int force) {
+        k_reclassify<T, LF, LG><<<grid_for(ncell_, 256), 256, 0, st>>>(d_, ph_, form, force);
+    }
+
+    void enqueue_lists(cudaStream_t st, int force) {
         for (int which = 0; which < (d_.use_fl ? 3 : 2); ++which) {
             k_count<T, LG><<<nchunks_, 256, 0, st>>>(d_, which, force);
             k_scan<T><<<1, 1024, 0, st>>>(d_, nchunks_, which, force);
             k_write_lists<T, LG><<<nchunks_, 256, 0, st>>>(d_, ph_, which, force);
         }
+    }
+
+    // Numbering of the stored set into (cmap_out, cid_out, ns_out): range
+    // codes from the current classes, then per range count / scan / write.
+    // go: null (unconditional) or a device flag the kernels test first.
+    void enqueue_numbering(cudaStream_t st, int* cmap_out, int* cid_out, int* ns_out, const int* go) {
+        k_sp_mark<T, LG><<<grid_for(ncell_, 256), 256, 0, st>>>(d_, d_.scode, go);
+        for (int r = 0; r < 3; ++r) {
+            k_sp_count<T><<<nchunks_, 256, 0, st>>>(d_, d_.scode, r, go);
+            k_sp_scan<T><<<1, 1024, 0, st>>>(d_, nchunks_, r, d_.stot, go);
+            k_sp_write<T><<<nchunks_, 256, 0, st>>>(d_, d_.scode, r, d_.stot, cmap_out, cid_out, go);
+        }
+        k_sp_total<T><<<1, 1, 0, st>>>(d_, d_.stot, ns_out, go);
+    }
+
+    // Creation of the active-cell layout: count the stored set, size and
+    // allocate the population storage, number the cells, build the tables.
+    int build_stored(std::string& err) {
+        constexpr int QF = LF::Q > 0 ? LF::Q : 0, QG = LG::Q;
+        using LS = typename Stencil<LF, LG>::L;
+        k_sp_mark<T, LG><<<grid_for(ncell_, 256), 256, 0, own_>>>(d_, d_.scode, nullptr);
+        for (int r = 0; r < 3; ++r) {
+            k_sp_count<T><<<nchunks_, 256, 0, own_>>>(d_, d_.scode, r, nullptr);
+            k_sp_scan<T><<<1, 1024, 0, own_>>>(d_, nchunks_, r, d_.stot, nullptr);
+        }
+        LB_CUDA(cudaGetLastError());
+        int tot[3] = {0, 0, 0};
+        LB_CUDA(cudaMemcpyAsync(tot, d_.stot, 3 * sizeof(int), cudaMemcpyDeviceToHost, own_));
+        LB_CUDA(cudaStreamSynchronize(own_));
+        const long long ns = (long long)tot[0] + tot[1] + tot[2];
+        // With phase change the stored set can grow (dissolution) up to the
+        // whole grid; the storage is sized for that, so a repacking can never
+        // run out of room (it costs memory only: the sweeps touch the stored
+        // cells alone).  Without phase change the set never changes.
+        long long cap = prm_.phase_change ? ncell_ : ns;
+        cap = std::max<long long>(64, ((cap + 63) / 64) * 64);
+        ns0_ = ns;
+        if ((long long)std::max(QF, QG) * cap >= (1LL << 32) || (long long)(LS::Q - 1) * cap >= (1LL << 40)) {
+            err = "stored set too large for 32-bit population indices";
+            return 1;
+        }
+        d_.cap_s = cap;
+        popn_ = cap;
+        if (QF) LB_CUDA(dalloc(&d_.F, (size_t)QF * cap));
+        LB_CUDA(dalloc(&d_.G, (size_t)QG * cap));
+        if (QF) LB_CUDA(cudaMemset(d_.F, 0, (size_t)QF * cap * sizeof(T)));
+        LB_CUDA(cudaMemset(d_.G, 0, (size_t)QG * cap * sizeof(T)));
+        LB_CUDA(dalloc(&d_.cid, (size_t)cap));
+        LB_CUDA(dalloc(&d_.nwc, (size_t)cap));
+        LB_CUDA(dalloc(&d_.nbt, (size_t)(LS::Q - 1) * cap));
+        LB_CUDA(cudaMemset(d_.nwc, 0, cap * sizeof(uint32_t)));
+        if (prm_.phase_change) {
+            LB_CUDA(dalloc(&d_.cid2, (size_t)cap));
+            if (QF) LB_CUDA(dalloc(&d_.F2, (size_t)QF * cap));
+            LB_CUDA(dalloc(&d_.G2, (size_t)QG * cap));
+        }
+        enqueue_numbering(own_, d_.cmap, d_.cid, d_.ns, nullptr);
+        k_sp_tables<T, LF, LG><<<grid_for(cap, 256), 256, 0, own_>>>(d_, nullptr);
         LB_CUDA(cudaGetLastError());
         return 0;
+    }
+
+    // Repacking inside the step graph: every kernel returns at once unless a
+    // reclassification found a cell that needs storage it does not have.
+    void enqueue_repack(cudaStream_t st) {
+        k_sp_clear2<T><<<grid_for(d_.geo.NP, 256), 256, 0, st>>>(d_);
+        enqueue_numbering(st, d_.cmap2, d_.cid2, d_.ns2, d_.repack);
+        k_sp_gather<T, LF, LG><<<grid_for(d_.cap_s, 256), 256, 0, st>>>(d_, ph_);
+        k_sp_commit<T, LF, LG><<<grid_for(d_.geo.NP, 256), 256, 0, st>>>(d_);
+        k_sp_commit_end<T><<<1, 1, 0, st>>>(d_);
+        k_sp_tables<T, LF, LG><<<grid_for(d_.cap_s, 256), 256, 0, st>>>(d_, d_.repack);
+        k_sp_repack_done<T><<<1, 1, 0, st>>>(d_);
     }
 
     // One time step; with `ev` (5 events) the kernel groups are bracketed by
@@ -745,7 +865,11 @@ class Engine final : public ISim {
                      const Dev<T>* dv = nullptr) {
         const Dev<T>& d_ = dv ? *dv : this->d_;
         const Geo& g = d_.geo;
+        const bool sp = d_.sparse != 0;
         dim3 grid((g.nx + FLUID_BLOCK - 1) / FLUID_BLOCK, g.ny, g.nz);
+        // one thread per stored cell at creation; the sweep strides over any
+        // growth of the set
+        const int gsp = sp ? (int)std::max<long long>(1, (ns0_ + FLUID_BLOCK - 1) / FLUID_BLOCK) : 1;
         if (ev) LB_CUDA(cudaEventRecord(ev[0], st));
         // Without per-group timing the boundary list and the fluid ends run
         // on a second stream beside the fluid sweep: the three kernels touch
@@ -755,12 +879,14 @@ class Engine final : public ISim {
         if (fork) {
             LB_CUDA(cudaEventRecord(fork_, st));
             LB_CUDA(cudaStreamWaitEvent(aux_, fork_, 0));
-            if (odd) k_bound<T, LG, true><<<bgrid_, LIST_BLOCK, 0, aux_>>>(d_, ph_, pt_);
-            else k_bound<T, LG, false><<<bgrid_, LIST_BLOCK, 0, aux_>>>(d_, ph_, pt_);
+            launch_bound(aux_, odd, d_);
             k_fend<T, LG><<<fgrid_, LIST_BLOCK, 0, aux_>>>(d_, ph_);
             LB_CUDA(cudaEventRecord(join_, aux_));
         }
-        if (d_.use_fl) {
+        if (sp) {
+            if (odd) k_fluid_sp<T, LF, LG, true><<<gsp, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_);
+            else k_fluid_sp<T, LF, LG, false><<<gsp, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_);
+        } else if (d_.use_fl) {
             const int gl = (int)((d_.cap_fl + FLUID_BLOCK - 1) / FLUID_BLOCK);
             if (odd) k_fluid_list<T, LF, LG, true><<<gl, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_);
             else k_fluid_list<T, LF, LG, false><<<gl, FLUID_BLOCK, 0, st>>>(d_, ph_, pt_);
@@ -772,20 +898,34 @@ class Engine final : public ISim {
             LB_CUDA(cudaStreamWaitEvent(st, join_, 0));
         } else {
             LB_CUDA(cudaEventRecord(ev[1], st));
-            if (odd) k_bound<T, LG, true><<<bgrid_, LIST_BLOCK, 0, st>>>(d_, ph_, pt_);
-            else k_bound<T, LG, false><<<bgrid_, LIST_BLOCK, 0, st>>>(d_, ph_, pt_);
+            launch_bound(st, odd, d_);
             LB_CUDA(cudaEventRecord(ev[2], st));
             k_fend<T, LG><<<fgrid_, LIST_BLOCK, 0, st>>>(d_, ph_);
             LB_CUDA(cudaEventRecord(ev[3], st));
         }
         if (ph_.phase_change) {
             const int eg = 152 * 2;
-            const int lo = odd ? 1 : 0;
+            // The event kernels read and write post-collision populations.
+            // Dense layout: at their AA positions after this step.  Active-
+            // cell layout: in the even-step form (each cell's own slots);
+            // after an odd step the links of the event region are swapped
+            // into that form first, and back once the classes have changed.
+            const int form = sp ? 0 : (odd ? 1 : 0);
             k_ev_mark<T><<<eg, 256, 0, st>>>(d_);
-            k_ev_compute<T, LF, LG><<<eg, 256, 0, st>>>(d_, ph_, lo);
-            k_ev_apply_self<T, LF, LG><<<eg, 256, 0, st>>>(d_, ph_, lo);
-            k_ev_neighbours<T, LG><<<eg, 256, 0, st>>>(d_, ph_, lo);
-            if (rebuild(st, lo, 0, err)) return 2;
+            if (sp && odd) {
+                k_sp_rmark<T, LG><<<eg, 256, 0, st>>>(d_);
+                k_sp_swap<T, LF, LG><<<eg, 256, 0, st>>>(d_);
+            }
+            k_ev_compute<T, LF, LG><<<eg, 256, 0, st>>>(d_, ph_, form);
+            k_ev_apply_self<T, LF, LG><<<eg, 256, 0, st>>>(d_, ph_, form);
+            k_ev_neighbours<T, LG><<<eg, 256, 0, st>>>(d_, ph_, form);
+            enqueue_reclassify(st, form, 0);
+            if (sp) enqueue_repack(st);
+            if (sp && odd) {
+                k_sp_swap<T, LF, LG><<<eg, 256, 0, st>>>(d_);
+                k_sp_rreset<T, LG><<<eg, 256, 0, st>>>(d_);
+            }
+            enqueue_lists(st, 0);
             k_ev_reset<T><<<eg, 256, 0, st>>>(d_);
             k_step_end<T><<<1, 1, 0, st>>>(d_);
         }
@@ -794,9 +934,43 @@ class Engine final : public ISim {
         return 0;
     }
 
+    void launch_bound(cudaStream_t st, bool odd, const Dev<T>& d) {
+        if (d.sparse) {
+            if (odd) k_bound<T, LF, LG, true, true><<<bgrid_, LIST_BLOCK, 0, st>>>(d, ph_, pt_);
+            else k_bound<T, LF, LG, false, true><<<bgrid_, LIST_BLOCK, 0, st>>>(d, ph_, pt_);
+        } else {
+            if (odd) k_bound<T, LF, LG, true, false><<<bgrid_, LIST_BLOCK, 0, st>>>(d, ph_, pt_);
+            else k_bound<T, LF, LG, false, false><<<bgrid_, LIST_BLOCK, 0, st>>>(d, ph_, pt_);
+        }
+    }
+
    public:
-    // Number of kernel launches of one step.
-    int launches_per_step() const override { return 3 + (ph_.phase_change ? 5 + 3 * 2 + 2 + 1 : 0); }
+    // Number of kernel launches of one step (mean of an even and an odd step).
+    int launches_per_step() const override {
+        int n = 3;
+        if (ph_.phase_change) {
+            n += 4 + 1 + 3 * (d_.use_fl ? 3 : 2) + 2;  // events, reclassification, lists, reset + step end
+            if (d_.sparse) n += 1 + (1 + 9 + 1) + 5 + 2;  // repacking (conditional) + swaps of odd steps / 2
+        }
+        return n;
+    }
+
+    int layout_info(int64_t* out, std::string& err) override {
+        LB_CUDA(cudaStreamSynchronize(last_stream_ ? last_stream_ : own_));
+        constexpr int QF = LF::Q > 0 ? LF::Q : 0, QG = LG::Q;
+        out[0] = d_.sparse ? LBRBC_LAYOUT_SPARSE : LBRBC_LAYOUT_DENSE;
+        out[1] = d_.geo.NP;
+        out[2] = 0;
+        if (d_.sparse) {
+            int h[2] = {0, 0};
+            LB_CUDA(cudaMemcpy(&h[0], d_.ns, sizeof(int), cudaMemcpyDeviceToHost));
+            LB_CUDA(cudaMemcpy(&h[1], d_.nrepack, sizeof(int), cudaMemcpyDeviceToHost));
+            out[1] = h[0];
+            out[2] = h[1];
+        }
+        out[3] = (int64_t)(QF + QG) * popn_ * (int64_t)sizeof(T);
+        return 0;
+    }
 
     // Run n steps without graphs, timing each kernel group with CUDA events on
     // the stream the kernels run on; ms[g] = mean duration of group g.
@@ -897,6 +1071,9 @@ class Engine final : public ISim {
     bool graphs_ = false;
     bool batched_ = false;
     bool force_list_ = false;
+    bool force_dense_ = false;
+    long long popn_ = 0;  // population slots per direction (padded grid or stored-cell capacity)
+    long long ns0_ = 0;   // stored cells at creation (active-cell layout)
     double lane_eff_ = 1.0;
     std::vector<void*> allocs_;
 };

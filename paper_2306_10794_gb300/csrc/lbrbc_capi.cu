@@ -56,6 +56,7 @@ std::string lbrbc_validate_params(const lbrbc_params& p) {
     if (p.precision != LBRBC_FP32 && p.precision != LBRBC_FP64) return "precision must be FP32 or FP64";
     if (!(p.rho_init > 0.0)) return "rho_init must be positive";
     if (p.event_log_capacity < 0) return "event_log_capacity must be >= 0";
+    if (p.layout < LBRBC_LAYOUT_AUTO || p.layout > LBRBC_LAYOUT_SPARSE) return "layout must be AUTO, DENSE or SPARSE";
     return "";
 }
 
@@ -162,6 +163,13 @@ lbrbc_status lbrbc_info(lbrbc_sim* sim, int64_t* out) {
     out[1] = sim->impl->boundary_cells();
     out[2] = sim->impl->launches_per_step();
     return LBRBC_OK;
+}
+
+lbrbc_status lbrbc_layout_info(lbrbc_sim* sim, int64_t* out) {
+    if (!sim || !out) return fail(sim, LBRBC_ERR_ARG, "NULL argument");
+    std::string err;
+    int rc = sim->impl->layout_info(out, err);
+    return rc ? fail(sim, rc, err) : LBRBC_OK;
 }
 
 lbrbc_status lbrbc_check(lbrbc_sim* sim) {

@@ -30,6 +30,7 @@ class ISim {
     virtual int adjoint(int64_t n, double* J, double* dk, double* dceq, double* dk_field, std::string& err) = 0;
     virtual long long fluid_cells() const = 0;
     virtual long long boundary_cells() const = 0;
+    virtual int layout_info(int64_t* out, std::string& err) = 0;
 };
 
 // Many independent domains stepped together (same lattices and precision).

@@ -22,6 +22,7 @@ LBRBC_ERR_TIMEOUT, LBRBC_ERR_STATE, LBRBC_ERR_UNSUPPORTED = 4, 5, 6
 BC = {"periodic": 0, "wall": 1, "open": 2}
 SCHEME = {"new": 0, "verhaeghe": 1, "patel_ju": 2, "anti_bb": 3}
 PRECISION = {"fp32": 0, "fp64": 1}
+LAYOUT = {"auto": 0, "dense": 1, "sparse": 2}
 CLASS_FLUID, CLASS_BOUND, CLASS_SOLID = 0, 1, 2
 EV_DISSOLVE, EV_PRECIPITATE = 1, 2
 
@@ -36,7 +37,7 @@ class lbrbc_params(ctypes.Structure):
         ("magic_solute", ctypes.c_double), ("rest_fraction", ctypes.c_double), ("k_r", ctypes.c_double),
         ("c_eq", ctypes.c_double), ("molar_volume", ctypes.c_double), ("c_init", ctypes.c_double),
         ("rho_init", ctypes.c_double), ("c_dirichlet", ctypes.c_double), ("c_inlet", ctypes.c_double),
-        ("u_inlet", ctypes.c_double), ("rho_outlet", ctypes.c_double),
+        ("u_inlet", ctypes.c_double), ("rho_outlet", ctypes.c_double), ("layout", ctypes.c_int),
     ]
 
 
@@ -55,7 +56,7 @@ _lib = None
 
 EXPORTED = ["lbrbc_create", "lbrbc_step", "lbrbc_fields", "lbrbc_classes", "lbrbc_mass_ledger",
             "lbrbc_mass_ledger_noalloc", "lbrbc_noalloc_size_check",
-            "lbrbc_events", "lbrbc_adjoint", "lbrbc_profile_step", "lbrbc_info", "lbrbc_check", "lbrbc_last_error",
+            "lbrbc_events", "lbrbc_adjoint", "lbrbc_profile_step", "lbrbc_info", "lbrbc_layout_info", "lbrbc_check", "lbrbc_last_error",
             "lbrbc_destroy", "lbrbc_batch_create", "lbrbc_batch_step", "lbrbc_batch_autotune",
             "lbrbc_batch_info", "lbrbc_batch_domain", "lbrbc_batch_last_error", "lbrbc_batch_destroy"]
 
@@ -94,6 +95,8 @@ def load(path: str = LIB_PATH):
     lib.lbrbc_profile_step.argtypes = [vp, ctypes.c_int64, vp, dp, P(ctypes.c_int64)]
     lib.lbrbc_info.restype = ctypes.c_int
     lib.lbrbc_info.argtypes = [vp, P(ctypes.c_int64)]
+    lib.lbrbc_layout_info.restype = ctypes.c_int
+    lib.lbrbc_layout_info.argtypes = [vp, P(ctypes.c_int64)]
     lib.lbrbc_check.restype = ctypes.c_int
     lib.lbrbc_check.argtypes = [vp]
     lib.lbrbc_last_error.restype = ctypes.c_char_p
@@ -222,6 +225,14 @@ def lbrbc_info(handle):
     return dict(fluid_cells=out[0], boundary_cells=out[1], launches_per_step=out[2])
 
 
+def lbrbc_layout_info(handle):
+    lib = load()
+    out = (ctypes.c_int64 * 4)()
+    _check(lib, handle, lib.lbrbc_layout_info(handle, out))
+    return dict(layout={1: "dense", 2: "sparse"}.get(out[0], str(out[0])), stored_cells=out[1], repacks=out[2],
+                population_bytes=out[3])
+
+
 def lbrbc_check(handle):
     lib = load()
     _check(lib, handle, lib.lbrbc_check(handle))
@@ -241,11 +252,17 @@ DEFAULTS = dict(dim=3, nx=8, ny=8, nz=8, flow_q=19, solute_q=7, bc=("periodic", 
                 scheme="new", phase_change=0, precision="fp32", event_log_capacity=0, tau_flow=0.8,
                 magic_flow=-1.0, tau_solute=0.8, magic_solute=-1.0, rest_fraction=-1.0, k_r=0.0, c_eq=0.0,
                 molar_volume=1.0, c_init=0.0, rho_init=1.0, c_dirichlet=0.0, c_inlet=0.0, u_inlet=0.0,
-                rho_outlet=1.0)
+                rho_outlet=1.0, layout="auto")
 
 
 def make_params(p: dict) -> lbrbc_params:
+    """ctypes parameter block from a dict (missing keys take DEFAULTS).  When
+    the dict names no layout, the environment variable LBRBC_LAYOUT (auto,
+    dense or sparse) chooses it, so a whole test run can be repeated on
+    either population layout."""
     q = dict(DEFAULTS)
+    if "layout" not in p and os.environ.get("LBRBC_LAYOUT"):
+        q["layout"] = os.environ["LBRBC_LAYOUT"]
     q.update(p)
     s = lbrbc_params()
     for k in ("dim", "nx", "ny", "nz", "flow_q", "solute_q", "phase_change", "event_log_capacity"):
@@ -256,6 +273,7 @@ def make_params(p: dict) -> lbrbc_params:
         s.bc[a] = BC[q["bc"][a]] if isinstance(q["bc"][a], str) else int(q["bc"][a])
     s.scheme = SCHEME[q["scheme"]] if isinstance(q["scheme"], str) else int(q["scheme"])
     s.precision = PRECISION[q["precision"]] if isinstance(q["precision"], str) else int(q["precision"])
+    s.layout = LAYOUT[q["layout"]] if isinstance(q["layout"], str) else int(q["layout"])
     for k in ("tau_flow", "magic_flow", "tau_solute", "magic_solute", "rest_fraction", "k_r", "c_eq",
               "molar_volume", "c_init", "rho_init", "c_dirichlet", "c_inlet", "u_inlet", "rho_outlet"):
         setattr(s, k, float(q[k]))
@@ -329,6 +347,9 @@ class Sim:
 
     def info(self) -> dict:
         return lbrbc_info(self._h)
+
+    def layout_info(self) -> dict:
+        return lbrbc_layout_info(self._h)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -57,7 +57,7 @@ def build(force: bool = False) -> str:
         os.makedirs(_BUILD, exist_ok=True)
         tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-shared", "-fPIC",
-                               "-o", tmp, _SRC, "-lm"])
+                               "-o", tmp, _SRC, "-lm", "-lpthread"])
         os.replace(tmp, _LIB_PATH)
         return _LIB_PATH
 
@@ -72,6 +72,7 @@ def _load():
     lib.orc_create.restype = ctypes.c_void_p
     lib.orc_create.argtypes = [P(_Params), u8p, dp, dp, dp, dp, dp]
     lib.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_long]
+    lib.orc_set_threads.argtypes = [ctypes.c_void_p, ctypes.c_int]
     lib.orc_fields.argtypes = [ctypes.c_void_p, dp, dp, dp, dp]
     lib.orc_classes.argtypes = [ctypes.c_void_p, u8p]
     lib.orc_normals.argtypes = [ctypes.c_void_p, dp]
@@ -153,6 +154,12 @@ class OracleSim:
 
     def step(self, n: int = 1):
         self._lib.orc_step(self._h, int(n))
+
+    def set_threads(self, n: int):
+        """Run the per-cell loop as n z-slabs on n host threads (for timing
+        the oracle on all cores; fields are unchanged, the ledger sums are
+        added per slab)."""
+        self._lib.orc_set_threads(self._h, int(n))
 
     def fields(self):
         """(u[z,y,x,3], rho, c, phi) of the current post-collision state."""

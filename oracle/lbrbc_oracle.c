@@ -29,9 +29,10 @@
  *      (precipitation) with redistribution (Sec. 2.4).
  * Where the paper is silent the reading used is stated next to the code.
  *
- * Compile: gcc -O2 -std=c99 -ffp-contract=off -shared -fPIC -o liblbrbc_oracle.so lbrbc_oracle.c -lm
+ * Compile: gcc -O2 -std=c99 -ffp-contract=off -shared -fPIC -o liblbrbc_oracle.so lbrbc_oracle.c -lm -lpthread
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -209,6 +210,7 @@ typedef struct {
     double *C, *rho;        /* per-node moments of this step            */
     double unpaid, dirichlet_in, open_in, reacted_total;
     long step;
+    int nthreads;           /* z-slabs of the per-cell loop (timing only)  */
     long nev, capev;
     long *ev_step, *ev_node;
     int *ev_kind;
@@ -531,7 +533,14 @@ static void phase_change(orc_sim *s)
 /* ------------------------------------------------------------------ */
 /* One time step                                                       */
 /* ------------------------------------------------------------------ */
-static void one_step(orc_sim *s)
+/* Accumulators of the ledger terms summed over cells. */
+typedef struct {
+    double *open_in, *dirichlet_in, *reacted;
+} orc_acc;
+
+/* Steps 1-4 of one time step (streaming, reactive boundary condition,
+ * moments, collision, per-cell ledger) for the cells with z0 <= z < z1. */
+static void cells_slab(orc_sim *s, int z0, int z1, orc_acc acc)
 {
     const orc_params *p = &s->p;
     long N = s->N;
@@ -543,7 +552,7 @@ static void one_step(orc_sim *s)
     double tg_anti = p->tau_solute, tg_sym = trt_g ? tau_other(p->tau_solute, p->magic_solute) : p->tau_solute;
     double gamma = p->tau_solute / (p->tau_solute - 0.5);
 
-    for (int z = 0; z < p->nz; ++z)
+    for (int z = z0; z < z1; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
                 long id = IDX(s, x, y, z);
@@ -606,10 +615,10 @@ static void one_step(orc_sim *s)
                     if (st == NB_IN && s->cls[src] != ORC_SOLID) g[i] = s->gpost[i * N + src];
                     else if (st == NB_INLET && s->cls[id] == ORC_FLUID) {
                         g[i] = -bb + 2.0 * G->w[i] * p->c_inlet;   /* anti-bounce-back, C = c_inlet */
-                        s->open_in += g[i] - bb;
+                        *acc.open_in += g[i] - bb;
                     } else if (st == NB_OUTLET && s->cls[id] == ORC_FLUID) {
                         g[i] = -bb + 2.0 * G->w[i] * Cold;        /* zero-gradient outlet */
-                        s->open_in += g[i] - bb;
+                        *acc.open_in += g[i] - bb;
                     } else g[i] = bb;
                 }
                 if (s->cls[id] == ORC_BOUND) {
@@ -648,10 +657,10 @@ static void one_step(orc_sim *s)
                     }
                     double Msum = 0.0;
                     for (int o = 1; o < qg; ++o) Msum += s->mlink[o * N + id];
-                    if (s->kind[id] == ORC_KIND_DIRICHLET) s->dirichlet_in += Msum;
+                    if (s->kind[id] == ORC_KIND_DIRICHLET) *acc.dirichlet_in += Msum;
                     else {
                         s->M[id] = Msum;
-                        s->reacted_total += Msum;
+                        *acc.reacted += Msum;
                     }
                     u[0] = u[1] = u[2] = 0.0;
                 }
@@ -662,6 +671,63 @@ static void one_step(orc_sim *s)
                 collide(G, g, geq, trt_g, tg_sym, tg_anti);
                 for (int i = 0; i < qg; ++i) s->gnew[i * N + id] = g[i];
             }
+
+}
+
+/* The per-cell loop may run as z-slabs on several host threads (used only to
+ * time the oracle on all cores): every cell reads the previous step's state
+ * and writes only its own entries, and each slab sums its ledger terms in
+ * its own accumulators, added in slab order afterwards.  With one thread the
+ * loop and its sums are exactly the single-slab loop above. */
+typedef struct {
+    orc_sim *s;
+    int z0, z1;
+    double open_in, dirichlet_in, reacted;
+} orc_slab;
+
+static void *slab_main(void *arg)
+{
+    orc_slab *a = (orc_slab *)arg;
+    orc_acc acc = {&a->open_in, &a->dirichlet_in, &a->reacted};
+    cells_slab(a->s, a->z0, a->z1, acc);
+    return NULL;
+}
+
+static void cells_all(orc_sim *s)
+{
+    int nt = s->nthreads > 1 ? s->nthreads : 1;
+    if (nt > s->p.nz) nt = s->p.nz;
+    if (nt <= 1) {
+        orc_acc acc = {&s->open_in, &s->dirichlet_in, &s->reacted_total};
+        cells_slab(s, 0, s->p.nz, acc);
+        return;
+    }
+    orc_slab *sl = (orc_slab *)calloc(nt, sizeof(orc_slab));
+    pthread_t *th = (pthread_t *)calloc(nt, sizeof(pthread_t));
+    for (int t = 0; t < nt; ++t) {
+        sl[t].s = s;
+        sl[t].z0 = (int)((long)s->p.nz * t / nt);
+        sl[t].z1 = (int)((long)s->p.nz * (t + 1) / nt);
+        pthread_create(&th[t], NULL, slab_main, &sl[t]);
+    }
+    for (int t = 0; t < nt; ++t) pthread_join(th[t], NULL);
+    for (int t = 0; t < nt; ++t) {
+        s->open_in += sl[t].open_in;
+        s->dirichlet_in += sl[t].dirichlet_in;
+        s->reacted_total += sl[t].reacted;
+    }
+    free(sl);
+    free(th);
+}
+
+static void one_step(orc_sim *s)
+{
+    const orc_params *p = &s->p;
+    long N = s->N;
+    const orc_lat *G = &s->LG;
+    int qg = G->q;
+
+    cells_all(s);
 
     /* Eq. solidFractionUpdate, adjacent growth: dissolution lowers phi of the
      * boundary cell; precipitation raises phi of the fluid cells at the ends of
@@ -693,6 +759,12 @@ static void one_step(orc_sim *s)
     t = s->fpost; s->fpost = s->fnew; s->fnew = t;
     t = s->gpost; s->gpost = s->gnew; s->gnew = t;
     s->step++;
+}
+
+/* Number of host threads of the per-cell loop (1: the plain loop). */
+void orc_set_threads(void *h, int n)
+{
+    ((orc_sim *)h)->nthreads = n < 1 ? 1 : n;
 }
 
 int orc_step(void *h, long n)

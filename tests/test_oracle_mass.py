@@ -455,3 +455,22 @@ def test_corner_precipitations_split_by_post_event_normals_by_hand():
     assert c[0, 2, 2] == pytest.approx(c_ref[0, 2, 2], rel=1e-14)
     assert phi[0, 3, 2] == 1.0 and phi[0, 2, 3] == 1.0
     assert _invariant(s.ledger()) == pytest.approx(_invariant(L0), rel=1e-13)
+
+
+def test_threaded_cell_loop_changes_nothing_but_the_sum_order():
+    # the all-cores timing mode of the oracle: z-slabs on host threads
+    shape = (13, 10, 24)
+    mask = workloads.sphere_pack(shape, 0.55, 2.0, 3.5, seed=9, periodic=(False, True, True), buffer_x=2)
+    p = dict(dim=3, nx=24, ny=10, nz=13, flow_q=19, solute_q=7, bc=("open", "periodic", "periodic"), tau_flow=0.8,
+             magic_flow=3.0 / 16.0, tau_solute=0.9, k_r=0.2, c_eq=1.0, c_init=2.0, c_inlet=2.0, u_inlet=0.02,
+             molar_volume=0.3, phase_change=1)
+    a, b = oracle.OracleSim(p, mask), oracle.OracleSim(p, mask)
+    b.set_threads(4)
+    a.step(30)
+    b.step(30)
+    for x, y in zip(a.fields(), b.fields()):
+        assert np.array_equal(x, y)
+    assert a.events().tolist() == b.events().tolist()
+    La, Lb = a.ledger(), b.ledger()
+    for k in ("open_in", "reacted", "dirichlet_in"):
+        assert Lb[k] == pytest.approx(La[k], rel=1e-12, abs=1e-15), k

@@ -2,17 +2,21 @@
 """Throughput of the coupled LBM step with the general local reactive
 boundary condition on one GB300 (or N independent replicas under torchrun).
 
-Workload: 3D D3Q19 flow + D3Q7 solute in a 256x128x128 slab channel whose
-walls are tilted 30 degrees against the grid, plane-Poiseuille inflow at
-Re = 1, Pe = 10 (rest fraction), Da = 1, inlet c = 1, c_eq = 0.5, FP32
-populations with FP64 ledgers.  A step is one pass of the whole hot path:
-fluid stream-collide, reactive boundary condition + ledger + solid fraction
-on every wet boundary cell, and the precipitation-share gather.
+Default workload: 3D precipitation in a seeded sphere pack of 512^3 cells
+(porosity 0.4, radii U[8,16], periodic in y and z, 8 fluid layers at both
+open x ends), D3Q19 TRT flow at Re = 0.1, D3Q7 solute at Pe = 100 through
+the rest fraction, supersaturated inlet c = 2 c_eq, phase change on, FP32
+populations with FP64 ledgers and solid fractions.  A step is one pass of
+the whole hot path: fluid stream-collide, reactive boundary condition +
+ledger + solid fraction on every wet boundary cell, the precipitation-share
+gather, and the phase-change events with the rebuild of the lists.
+``--case channel`` runs the 256x128x128 tilted channel instead.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
-oracle on the same workload instead (bounded per-step samples).
+oracle on the same workload instead (bounded per-step samples, all cores).
 """
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -21,6 +25,7 @@ import statistics
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -29,13 +34,15 @@ sys.path.insert(0, ROOT)
 METRIC = "coupled MLUPS and % of HBM roofline at stated accuracy vs FP64; adjoint/forward cost"
 BYTES_PER_FLUID_CELL = {"fp32": 2 * (19 + 7) * 4, "fp64": 2 * (19 + 7) * 8}
 L2_BYTES = 129e6
+# cells of an oracle sample (about 420 B of host memory per cell)
+ORACLE_MAX_CELLS = 8_000_000
 
 
 def args_():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20000)
-    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--theta", type=float, default=30.0)
@@ -43,8 +50,13 @@ def args_():
     ap.add_argument("--da", type=float, default=1.0)
     ap.add_argument("--size", type=str, default="256x128x128")
     ap.add_argument("--pack-n", type=int, default=512, help="edge of the sphere-pack case")
-    ap.add_argument("--case", choices=["channel", "spherepack", "batch", "adjoint", "molins"], default="channel",
-                    help="channel: the headline workload; spherepack: 512^3 precipitation with phase change")
+    ap.add_argument("--case", choices=["channel", "spherepack", "batch", "adjoint", "molins"], default="spherepack",
+                    help="spherepack: the headline, 512^3 precipitation with phase change; channel: 256x128x128 "
+                         "tilted channel")
+    ap.add_argument("--layout", choices=["auto", "dense", "sparse"], default="auto",
+                    help="population layout of the library (auto: active cells in porous media)")
+    ap.add_argument("--accuracy-steps", type=int, default=None,
+                    help="steps of the FP32-vs-FP64 accuracy run (default: the case's run length)")
     ap.add_argument("--sweep", choices=["dense", "list"], default="dense",
                     help="fluid-cell sweep of the library (LBRBC_FLUID_SWEEP)")
     ap.add_argument("--domains", type=int, default=256, help="number of domains of --case batch")
@@ -62,12 +74,14 @@ def workload(a):
     if a.case == "spherepack":
         p, mask, extra = workloads.case_sphere_pack(n=a.pack_n)
         p["precision"] = a.precision
+        p["layout"] = a.layout
         name = ("3D precipitation in a seeded sphere pack %d^3, porosity 0.4, radii U[8,16], D3Q19 TRT flow "
                 "Re=0.1 + D3Q7 solute Pe=100 (rest fraction), c_in = 2 c_eq, phase change on, %s" % (a.pack_n, a.precision))
         return p, mask, extra, name
     nx, ny, nz = (int(v) for v in a.size.split("x"))
     p, mask, extra = workloads.case_channel(nx=nx, ny=ny, nz=nz, theta_deg=a.theta, Pe=a.pe, Da=a.da)
     p["precision"] = a.precision
+    p["layout"] = a.layout
     name = ("3D tilted channel %dx%dx%d, walls %g deg to the grid, D3Q19 TRT flow Re=1 + D3Q7 solute "
             "Pe=%g Da=%g (rest fraction), c_in=1 c_eq=0.5, %s" % (nx, ny, nz, a.theta, a.pe, a.da, a.precision))
     return p, mask, extra, name
@@ -77,21 +91,72 @@ def workload(a):
 # clocks during the timed region
 # ---------------------------------------------------------------------------
 class Clocks:
+    """SM clock, power and clock-event reasons while the timed region runs.
+    NVML (the driver's management library, read-only queries through ctypes)
+    is polled every 2 ms from a thread, so a timed region of tens of
+    milliseconds still gets samples; without NVML, nvidia-smi samples every
+    200 ms."""
+
+    # clock-event reason bits of the NVML API
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
-        self.index = index
+        self.index = self.nvml_index(index)
+        self.rows, self.stop_flag, self.thread, self.p = [], False, None, None
+        self.lib = self.dev = None
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            dev = ctypes.c_void_p()
+            if lib.nvmlInit_v2() == 0 and lib.nvmlDeviceGetHandleByIndex_v2(self.index, ctypes.byref(dev)) == 0:
+                self.lib, self.dev = lib, dev
+                self.reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                    getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+                mx = ctypes.c_uint()
+                self.max_mhz = float(mx.value) if lib.nvmlDeviceGetMaxClockInfo(dev, 1, ctypes.byref(mx)) == 0 else None
+                self.thread = threading.Thread(target=self._poll, daemon=True)
+                self.thread.start()
+                return
+        except Exception:
+            self.lib = None
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
-            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.Q,
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
                                        "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
                                       stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
 
+    @staticmethod
+    def nvml_index(local):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if ids and all(v.isdigit() for v in ids) and local < len(ids):
+            return int(ids[local])
+        return local
+
+    def _poll(self):
+        sm, rs, pw = ctypes.c_uint(), ctypes.c_ulonglong(), ctypes.c_uint()
+        while not self.stop_flag:
+            ok = self.lib.nvmlDeviceGetClockInfo(self.dev, 1, ctypes.byref(sm)) == 0
+            ok = ok and self.reasons_fn(self.dev, ctypes.byref(rs)) == 0
+            self.lib.nvmlDeviceGetPowerUsage(self.dev, ctypes.byref(pw))
+            if ok:
+                self.rows.append((float(sm.value), int(rs.value), pw.value / 1000.0))
+            time.sleep(0.002)
+
     def stop(self):
+        if self.thread is not None:
+            self.stop_flag = True
+            self.thread.join(timeout=5)
+            if not self.rows:
+                return None
+            sm = [r[0] for r in self.rows]
+            reasons = sorted({n for r in self.rows for b, n in self.REASONS.items() if r[1] & b})
+            return {"sm_mhz": statistics.median(sm), "sm_max_mhz": self.max_mhz, "reasons": reasons,
+                    "samples": len(self.rows), "power_w_max": max(r[2] for r in self.rows), "source": "nvml 2 ms"}
         if self.p is None:
             return None
         self.p.terminate()
@@ -114,7 +179,7 @@ class Clocks:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "source": "nvidia-smi 200 ms"}
 
 
 def measured_peak():
@@ -148,16 +213,18 @@ def fp64_ops_per_cell(kernel_src_hash, wkey):
     return float(t.group(1)), os.path.relpath(path, ROOT)
 
 
-def workload_key(a):
+def workload_key(a, layout):
     """Identifies the workload an ncu summary was taken on."""
-    return "%s-%s-%s-theta%g-pe%g-da%g-%s" % (a.case, a.size, a.precision, a.theta, a.pe, a.da, a.sweep)
+    if a.case == "spherepack":
+        return "spherepack-n%d-%s-%s" % (a.pack_n, a.precision, layout)
+    return "%s-%s-%s-theta%g-pe%g-da%g-%s-%s" % (a.case, a.size, a.precision, a.theta, a.pe, a.da, a.sweep, layout)
 
 
-def ncu_traffic(kernel_src_hash, wkey):
+def ncu_traffic(kernel_src_hash, wkey, fname):
     """DRAM bytes per launch of the fluid kernel from the committed ncu summary,
     if it was taken on the current kernel source and on this workload (else
     None)."""
-    path = os.path.join(ROOT, "profiles", "k_fluid_channel.md")
+    path = os.path.join(ROOT, "profiles", fname)
     try:
         txt = open(path).read()
     except OSError:
@@ -202,29 +269,31 @@ def aggregate(ms_local, units_local, dist=None, device=None):
 # ---------------------------------------------------------------------------
 # CPU oracle timing
 # ---------------------------------------------------------------------------
-def oracle_mlups(p, mask, extra, budget_s, max_steps=None):
-    """Run the FP64 oracle on (a bounded x-slab of) the workload; returns
-    (MLUPS, cores, sample description, steps, seconds)."""
+def oracle_mlups(p, mask, extra, budget_s, threads=1, max_steps=None):
+    """Run the FP64 oracle on (a bounded x-slab of) the workload on `threads`
+    host threads; returns (MLUPS, threads, sample description, steps, s)."""
     import numpy as np
 
     import oracle
 
     nz, ny, nx = mask.shape
+    q = {k: v for k, v in p.items() if k not in ("precision", "layout")}
     # calibrate on a thin slab
-    q = dict(p)
     cal_nx = min(nx, 8)
     q["nx"] = cal_nx
     o = oracle.OracleSim(q, np.ascontiguousarray(mask[:, :, :cal_nx]), **extra)
+    o.set_threads(threads)
     t0 = time.perf_counter()
     o.step(1)
     t_cal = time.perf_counter() - t0
     o.close()
     per_slab_col = t_cal / cal_nx
     steps = max_steps or 1
-    sub_nx = max(4, min(nx, int(budget_s / max(steps * per_slab_col, 1e-9))))
+    sub_nx = max(4, min(nx, int(budget_s / max(steps * per_slab_col, 1e-9)), ORACLE_MAX_CELLS // (ny * nz)))
     q["nx"] = sub_nx
     sub = np.ascontiguousarray(mask[:, :, :sub_nx])
     o = oracle.OracleSim(q, sub, **extra)
+    o.set_threads(threads)
     fluid = int((sub == 0).sum())
     done, t0 = 0, time.perf_counter()
     while True:
@@ -234,9 +303,16 @@ def oracle_mlups(p, mask, extra, budget_s, max_steps=None):
         if (max_steps and done >= max_steps) or (not max_steps and el >= budget_s):
             break
     o.close()
-    desc = "x-slab %dx%dx%d of the workload (first %d columns, inlet included), %d step(s)" % (
-        sub_nx, ny, nz, sub_nx, done)
-    return fluid * done / el / 1e6, 1, desc, done, el
+    desc = "x-slab %dx%dx%d of the workload (first %d columns, inlet included), %d step(s), %d thread(s)" % (
+        sub_nx, ny, nz, sub_nx, done, threads)
+    return fluid * done / el / 1e6, threads, desc, done, el
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
 
 
 def reference_arm(a):
@@ -253,18 +329,21 @@ def reference_arm(a):
     import oracle
 
     nz, ny, nx = mask.shape
-    q = dict(p)
+    cores = host_cores()
+    q = {k: v for k, v in p.items() if k not in ("precision", "layout")}
     cal_nx = min(nx, 8)
     q["nx"] = cal_nx
     o = oracle.OracleSim(q, np.ascontiguousarray(mask[:, :, :cal_nx]), **extra)
+    o.set_threads(cores)
     t0 = time.perf_counter()
     o.step(1)
     per_col = (time.perf_counter() - t0) / cal_nx
     o.close()
-    sub_nx = max(4, min(nx, int(per_step_budget / max(per_col, 1e-9))))
+    sub_nx = max(4, min(nx, int(per_step_budget / max(per_col, 1e-9)), ORACLE_MAX_CELLS // (ny * nz)))
     q["nx"] = sub_nx
     sub = np.ascontiguousarray(mask[:, :, :sub_nx])
     o = oracle.OracleSim(q, sub, **extra)
+    o.set_threads(cores)
     fluid = int((sub == 0).sum())
     o.step(W)
     t0 = time.perf_counter()
@@ -272,12 +351,12 @@ def reference_arm(a):
     el = time.perf_counter() - t0
     o.close()
     v = fluid * K / el / 1e6
-    sample = "x-slab %dx%dx%d of the workload per step (oracle FP64, single thread)" % (sub_nx, ny, nz)
+    sample = "x-slab %dx%dx%d of the workload per step (oracle FP64, %d threads: z-slabs)" % (sub_nx, ny, nz, cores)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": a.gpus, "steps": K,
             "warmup": W, "ms_per_step": el / K * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": name, "sample": sample, "fluid_cells_per_step": fluid},
-            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -490,6 +569,7 @@ def main():
     stream = torch.cuda.current_stream()
     sim = lbrbc.Sim(p, mask, **extra)
     info = sim.info()
+    lay = sim.layout_info()
     fluid = info["fluid_cells"]
     sim.step(W, stream=stream.cuda_stream)
     torch.cuda.synchronize()
@@ -520,17 +600,19 @@ def main():
     peak, peak_kind = measured_peak()
     achieved = bytes_launch / (kms[0] * 1e-3) / 1e9
     khash = kernel_hash()
-    traffic, traffic_src = ncu_traffic(khash, workload_key(a))
+    wkey = workload_key(a, lay["layout"])
+    traffic, traffic_src = ncu_traffic(khash, wkey, "k_fluid_pack512.md" if a.case == "spherepack"
+                                       else "k_fluid_channel.md")
     step_gbs = bytes_launch / (ms_max / K * 1e-3) / 1e9
     kname = "%s (fluid-cell stream-collide, D3Q19 + D3Q7)" % (
-        "k_fluid_list" if a.sweep == "list" else "k_fluid")
+        "k_fluid_sp" if lay["layout"] == "sparse" else ("k_fluid_list" if a.sweep == "list" else "k_fluid"))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": kname, "bytes_per_launch": bytes_launch, "ms_per_launch": kms[0],
                 "peak_kind": peak_kind, "traffic_source": traffic_src, "kernel_source_sha256": khash,
                 "step_algorithmic_gbs": step_gbs}
     if a.precision == "fp64":
         # the FP64 sweep is bound by GB300's FP64 rate, not by HBM
-        opc, osrc = fp64_ops_per_cell(khash, workload_key(a))
+        opc, osrc = fp64_ops_per_cell(khash, wkey)
         if opc is not None:
             gops = opc * fluid / (kms[0] * 1e-3) / 1e9
             roofline = {"bound": "alu", "achieved": gops, "peak": FP64_PEAK_GOPS, "unit": "G FP64 ops/s",
@@ -540,19 +622,40 @@ def main():
                         "kernel_source_sha256": khash,
                         "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak}}
 
-    # accuracy of this precision against the FP64 path (outside the timed region)
+    # accuracy of this precision against the FP64 path (outside the timed
+    # region), over the case's run length: the channel at full size for
+    # 20 000 steps; the sphere pack on a 128^3 pack of the same recipe for
+    # 50 000 steps (the full 512^3 run would take too long in FP64).  The
+    # FP64 path is matched against the oracle by the tests.
     acc = None
     if a.precision == "fp32" and not a.no_accuracy:
-        q = dict(p)
-        q["precision"] = "fp64"
-        s64 = lbrbc.Sim(q, mask, **extra)
-        s32 = lbrbc.Sim(p, mask, **extra)
-        s64.step(500)
-        s32.step(500)
-        u64, _, c64, _ = s64.fields()
-        u32, _, c32, _ = s32.fields()
-        rl2 = lambda x, y: float(np.sqrt(((x - y) ** 2).sum() / (y ** 2).sum()))
-        acc = {"steps": 500, "rel_l2_c": rl2(c32, c64), "rel_l2_u": rl2(u32, u64), "against": "FP64 CUDA path"}
+        from paper_2306_10794_gb300 import workloads
+
+        if a.case == "spherepack":
+            pa, ma, xa = workloads.case_sphere_pack(n=128)
+            pa["layout"] = a.layout
+            steps_acc = a.accuracy_steps or 50000
+            where = "128^3 sphere pack of the same recipe (seed 2306)"
+        else:
+            pa, ma, xa = p, mask, extra
+            steps_acc = a.accuracy_steps or 20000
+            where = "the workload itself"
+        pa = dict(pa, event_log_capacity=1 << 20)
+        s64 = lbrbc.Sim(dict(pa, precision="fp64"), ma, **xa)
+        s32 = lbrbc.Sim(dict(pa, precision="fp32"), ma, **xa)
+        s64.step(steps_acc, stream=stream.cuda_stream)
+        s32.step(steps_acc, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        s64.check()
+        s32.check()
+        u64, _, c64, phi64 = s64.fields()
+        u32, _, c32, phi32 = s32.fields()
+        ev64, ev32 = s64.events(), s32.events()
+        rl2 = lambda x, y: float(np.sqrt(((x - y) ** 2).sum() / max((y ** 2).sum(), 1e-300)))
+        acc = {"steps": steps_acc, "on": where, "rel_l2_c": rl2(c32, c64), "rel_l2_u": rl2(u32, u64),
+               "rel_l2_phi": rl2(phi32, phi64), "events_fp64": int(len(ev64)), "events_fp32": int(len(ev32)),
+               "events_identical": bool(len(ev64) == len(ev32) and np.array_equal(ev64, ev32)),
+               "against": "FP64 CUDA path"}
         s64.close()
         s32.close()
     sim.close()
@@ -582,8 +685,11 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        v, cores, desc, n, el = oracle_mlups(p, mask, extra, budget_s=12.0)
-        cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": desc}
+        nc = host_cores()
+        v, cores, desc, n, el = oracle_mlups(p, mask, extra, budget_s=10.0, threads=nc)
+        v1, _, desc1, _, _ = oracle_mlups(p, mask, extra, budget_s=10.0, threads=1)
+        cpu = {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": desc,
+               "single_thread": {"value": v1, "unit": "MLUPS", "cores": 1, "sample": desc1}}
 
     if rank == 0:
         line = {
@@ -592,9 +698,10 @@ def main():
             "dtype": "f32" if a.precision == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": name, "grid": list(mask.shape[::-1]), "fluid_cells": fluid,
                        "wet_boundary_cells": info["boundary_cells"], "parallelism": "replicas" if world > 1 else "1gpu",
+                       "layout": lay["layout"], "stored_cells": lay["stored_cells"],
                        "fluid_sweep": a.sweep,
                        "l2_policy": "no flush: populations %.2f GB resident > L2 %.0f MB" % (
-                           (26 * (4 if a.precision == "fp32" else 8) * mask.size) / 1e9, L2_BYTES / 1e6)},
+                           lay["population_bytes"] / 1e9, L2_BYTES / 1e6)},
             "roofline": roofline,
             "kernel_ms_per_step": {"fluid": kms[0], "boundary": kms[1], "fluid_ends": kms[2],
                                    "phase_change": kms[3]},

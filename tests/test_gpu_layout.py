@@ -32,11 +32,17 @@ def run(p, mask, steps, layout, **init):
     return out
 
 
+def by_step(ev):
+    # the log order within a step follows the atomics of the event queue:
+    # compare the events of each step as a set
+    return ev[np.lexsort((ev[:, 2], ev[:, 1], ev[:, 0]))] if len(ev) else ev
+
+
 def same(a, b):
     for x, y in zip(a["fields"], b["fields"]):
         assert np.array_equal(x, y)
     assert np.array_equal(a["classes"], b["classes"])
-    assert np.array_equal(a["events"], b["events"])
+    assert np.array_equal(by_step(a["events"]), by_step(b["events"]))
     for k in ("solute", "solid_over_vm", "unpaid", "dirichlet_in", "reacted"):
         assert a["ledger"][k] == b["ledger"][k], k
 
@@ -115,7 +121,7 @@ def test_repacking_matches_oracle():
         assert np.array_equal(g.classes(), o.classes())
         for a, b in zip(g.fields(), o.fields()):
             assert np.abs(a - b).max() < 1e-11
-        assert g.events().tolist() == o.events().tolist()
+        assert by_step(g.events()).tolist() == by_step(o.events()).tolist()
     assert g.layout_info()["repacks"] > 0
     lg, lo = g.ledger(), o.ledger()
     for k in ("solute", "solid_over_vm", "unpaid", "reacted"):

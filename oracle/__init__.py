@@ -73,6 +73,8 @@ def _load():
     lib.orc_create.argtypes = [P(_Params), u8p, dp, dp, dp, dp, dp]
     lib.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_long]
     lib.orc_set_threads.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.orc_adjoint.restype = ctypes.c_int
+    lib.orc_adjoint.argtypes = [ctypes.c_void_p, ctypes.c_long, dp, dp, dp, dp]
     lib.orc_fields.argtypes = [ctypes.c_void_p, dp, dp, dp, dp]
     lib.orc_classes.argtypes = [ctypes.c_void_p, u8p]
     lib.orc_normals.argtypes = [ctypes.c_void_p, dp]
@@ -154,6 +156,17 @@ class OracleSim:
 
     def step(self, n: int = 1):
         self._lib.orc_step(self._h, int(n))
+
+    def adjoint(self, n: int, field: bool = False):
+        """Advance n steps and return (J, dJ/dk_r, dJ/dc_eq, dJ/dk(x) or None):
+        J the reacted mass over those steps, the gradients by the oracle's
+        discrete adjoint (phase change must be off)."""
+        J, dk, dc = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        g = np.zeros(self.N) if field else None
+        rc = self._lib.orc_adjoint(self._h, int(n), ctypes.byref(J), ctypes.byref(dk), ctypes.byref(dc), _dptr(g))
+        if rc:
+            raise ValueError("oracle adjoint needs phase change off and n >= 1 (status %d)" % rc)
+        return J.value, dk.value, dc.value, (g.reshape(self.shape) if field else None)
 
     def set_threads(self, n: int):
         """Run the per-cell loop as n z-slabs on n host threads (for timing

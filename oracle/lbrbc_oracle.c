@@ -208,6 +208,7 @@ typedef struct {
     double *M;              /* per-node reacted mass of this step       */
     double *mlink;          /* per-node, per-direction ledger (solute q) */
     double *C, *rho;        /* per-node moments of this step            */
+    double *usol;           /* per-node velocity the solute collision used (3N) */
     double unpaid, dirichlet_in, open_in, reacted_total;
     long step;
     int nthreads;           /* z-slabs of the per-cell loop (timing only)  */
@@ -362,6 +363,7 @@ void *orc_create(const orc_params *p, const unsigned char *mask, const double *k
     s->mlink = (double *)calloc((size_t)qg * N, sizeof(double));
     s->C = (double *)calloc(N, sizeof(double));
     s->rho = (double *)calloc(N, sizeof(double));
+    s->usol = (double *)calloc(3 * N, sizeof(double));
     s->inlet_ux = (double *)calloc((size_t)s->p.ny * s->p.nz, sizeof(double));
     for (long i = 0; i < (long)s->p.ny * s->p.nz; ++i) s->inlet_ux[i] = inlet_ux ? inlet_ux[i] : p->u_inlet;
     if (kfield) {
@@ -667,6 +669,7 @@ static void cells_slab(orc_sim *s, int z0, int z1, orc_acc acc)
                 double C = 0.0;
                 for (int i = 0; i < qg; ++i) C += g[i];
                 s->C[id] = C;
+                for (int a = 0; a < 3; ++a) s->usol[3 * id + a] = u[a];
                 solute_equilibrium(G, C, u, geq);
                 collide(G, g, geq, trt_g, tg_sym, tg_anti);
                 for (int i = 0; i < qg; ++i) s->gnew[i * N + id] = g[i];
@@ -860,9 +863,172 @@ void orc_destroy(void *h)
     if (!s) return;
     free(s->kind); free(s->cls); free(s->fpost); free(s->gpost); free(s->fnew); free(s->gnew);
     free(s->phi); free(s->kfield); free(s->inlet_ux); free(s->normal); free(s->normal_ok);
-    free(s->M); free(s->mlink); free(s->C); free(s->rho);
+    free(s->M); free(s->mlink); free(s->C); free(s->rho); free(s->usol);
     free(s->ev_step); free(s->ev_node); free(s->ev_kind);
     free(s);
+}
+
+/* ------------------------------------------------------------------ */
+/* Discrete adjoint of the reacted mass (an extension: the paper has   */
+/* no gradient).                                                       */
+/* ------------------------------------------------------------------ */
+/* With phase change off and the flow independent of k_r and c_eq, one
+ * solute step maps the post-collision populations g affinely to the next
+ * ones:  h = pull(g) with the bounce-back and open-boundary rules (steps 1-2
+ * of the step above), h' = Eq. general_RBC on the links of boundary cells,
+ * g_new = collide(h') with the velocity u that step used, and the reacted
+ * mass grows by the ledger sum of (h'_o - h_o) over reactive links.  The
+ * adjoint below runs the forward steps, keeping g and u of every step, then
+ * walks back: lambda (dJ / d g of the later state) is pulled back through
+ * each stage by the transpose of that stage, written as the scatter of the
+ * stage's own gather, and the derivative of h'_o with respect to k and c_eq
+ * is collected on the way.  The collision matrix of a cell is taken by
+ * applying the oracle's own collide() to unit vectors (it is linear in h'
+ * for a fixed u).  Cells with k_r = 0 reflect without reacting under every
+ * scheme (as in the forward step), so they take no part in the k_r
+ * gradients.  Memory: (q + 3) N doubles per step. */
+
+/* k of a reactive link of cell id towards direction o and dk/dk_r; inf = 1
+ * for the anti-bounce-back limit (no k dependence). */
+static void link_k(const orc_sim *s, long id, int o, double kr, double *k, double *dkdkr, int *inf)
+{
+    const orc_lat *G = &s->LG;
+    double gamma = s->p.tau_solute / (s->p.tau_solute - 0.5);
+    double kap = kappa(s, id, G->e[o]);
+    *k = 0.0;
+    *dkdkr = 0.0;
+    *inf = 0;
+    switch (s->p.scheme) {
+    case ORC_NEW: *dkdkr = gamma * kap / G->cs2; break;
+    case ORC_VERHAEGHE: *dkdkr = kap / G->cs2; break;
+    case ORC_PATEL_JU:
+        if (kap > 0.0) *dkdkr = gamma / (G->cs2 * kap);
+        else *inf = 1;
+        break;
+    default: *inf = 1; break;
+    }
+    *k = *dkdkr * kr;
+}
+
+int orc_adjoint(void *h, long n, double *J, double *dJ_dk, double *dJ_dceq, double *dJ_dkfield)
+{
+    orc_sim *s = (orc_sim *)h;
+    if (s->p.phase_change || n < 1) return 1;
+    const orc_params *p = &s->p;
+    const orc_lat *G = &s->LG;
+    long N = s->N;
+    int qg = G->q;
+    int trt_g = p->magic_solute >= 0.0;
+    double tg_anti = p->tau_solute, tg_sym = trt_g ? tau_other(p->tau_solute, p->magic_solute) : p->tau_solute;
+    double *gs = (double *)malloc((size_t)n * qg * N * sizeof(double));
+    double *us = (double *)malloc((size_t)n * 3 * N * sizeof(double));
+    double *lam = (double *)calloc((size_t)qg * N, sizeof(double));
+    double *lam2 = (double *)calloc((size_t)qg * N, sizeof(double));
+    if (!gs || !us || !lam || !lam2) { free(gs); free(us); free(lam); free(lam2); return 2; }
+
+    double J0 = s->reacted_total;
+    for (long t = 0; t < n; ++t) {
+        memcpy(gs + (size_t)t * qg * N, s->gpost, (size_t)qg * N * sizeof(double));
+        one_step(s);
+        memcpy(us + (size_t)t * 3 * N, s->usol, (size_t)3 * N * sizeof(double));
+    }
+    *J = s->reacted_total - J0;
+    double gk = 0.0, gc = 0.0;
+    if (dJ_dkfield) memset(dJ_dkfield, 0, N * sizeof(double));
+
+    for (long t = n - 1; t >= 0; --t) {
+        const double *g = gs + (size_t)t * qg * N;
+        const double *u = us + (size_t)t * 3 * N;
+        memset(lam2, 0, (size_t)qg * N * sizeof(double));
+        for (int z = 0; z < p->nz; ++z)
+            for (int y = 0; y < p->ny; ++y)
+                for (int x = 0; x < p->nx; ++x) {
+                    long id = IDX(s, x, y, z);
+                    if (s->cls[id] == ORC_SOLID) continue;
+                    /* forward pull of this cell (kept to know h_obar) */
+                    double hh[19];
+                    int st[19];
+                    long src[19];
+                    double Cold = 0.0;
+                    for (int i = 0; i < qg; ++i) Cold += g[i * N + id];
+                    for (int i = 0; i < qg; ++i) {
+                        int me[3] = {-G->e[i][0], -G->e[i][1], -G->e[i][2]};
+                        st[i] = neighbour(s, x, y, z, me, &src[i]);
+                        double bb = g[G->opp[i] * N + id];
+                        if (st[i] == NB_IN && s->cls[src[i]] != ORC_SOLID) hh[i] = g[i * N + src[i]];
+                        else if (st[i] == NB_INLET && s->cls[id] == ORC_FLUID) hh[i] = -bb + 2.0 * G->w[i] * p->c_inlet;
+                        else if (st[i] == NB_OUTLET && s->cls[id] == ORC_FLUID) hh[i] = -bb + 2.0 * G->w[i] * Cold;
+                        else hh[i] = bb;
+                    }
+                    /* collision transpose: a_h'[j] = sum_i lambda_i M[i][j] */
+                    double uu[3] = {u[3 * id], u[3 * id + 1], u[3 * id + 2]};
+                    double ah[19];
+                    for (int j = 0; j < qg; ++j) {
+                        double col[19], geq[19];
+                        for (int i = 0; i < qg; ++i) col[i] = (i == j) ? 1.0 : 0.0;
+                        solute_equilibrium(G, 1.0, uu, geq);
+                        collide(G, col, geq, trt_g, tg_sym, tg_anti);
+                        double a = 0.0;
+                        for (int i = 0; i < qg; ++i) a += lam[i * N + id] * col[i];
+                        ah[j] = a;
+                    }
+                    /* reactive boundary condition and ledger, transposed */
+                    double ahh[19];
+                    for (int i = 0; i < qg; ++i) ahh[i] = ah[i];
+                    if (s->cls[id] == ORC_BOUND) {
+                        int dir = s->kind[id] == ORC_KIND_DIRICHLET;
+                        double kr = s->kfield ? s->kfield[id] : p->k_r;
+                        double cell_k = 0.0;
+                        for (int o = 1; o < qg; ++o) {
+                            long nb;
+                            if (neighbour(s, x, y, z, G->e[o], &nb) != NB_IN || s->cls[nb] != ORC_FLUID) continue;
+                            int ob = G->opp[o];
+                            /* h'_o replaced h_o: h_o reaches nothing but the ledger's -h_o */
+                            double a = ah[o];
+                            ahh[o] -= a;
+                            if (dir) {           /* h'_o = -h_obar + 2 w C_dir, not in J */
+                                ahh[ob] += -a;
+                                continue;
+                            }
+                            a += 1.0;            /* the ledger's +h'_o */
+                            ahh[o] += -1.0;      /* ... and its -h_o */
+                            if (kr == 0.0) {     /* inert: h'_o = h_obar */
+                                ahh[ob] += a;
+                                continue;
+                            }
+                            double k, dkdkr;
+                            int inf;
+                            link_k(s, id, o, kr, &k, &dkdkr, &inf);
+                            if (inf) {           /* h'_o = -h_obar + 2 w c_eq */
+                                ahh[ob] += -a;
+                                gc += a * 2.0 * G->w[o];
+                                continue;
+                            }
+                            ahh[ob] += a * (1.0 - k) / (1.0 + k);
+                            double dh = (2.0 * G->w[o] * p->c_eq - 2.0 * hh[ob]) / ((1.0 + k) * (1.0 + k));
+                            cell_k += a * dh * dkdkr;
+                            gc += a * k / (1.0 + k) * 2.0 * G->w[o];
+                        }
+                        gk += cell_k;
+                        if (dJ_dkfield) dJ_dkfield[id] += cell_k;
+                    }
+                    /* pull transposed: scatter onto the previous state */
+                    for (int i = 0; i < qg; ++i) {
+                        int ib = G->opp[i];
+                        if (st[i] == NB_IN && s->cls[src[i]] != ORC_SOLID) lam2[i * N + src[i]] += ahh[i];
+                        else if (st[i] == NB_INLET && s->cls[id] == ORC_FLUID) lam2[ib * N + id] -= ahh[i];
+                        else if (st[i] == NB_OUTLET && s->cls[id] == ORC_FLUID) {
+                            lam2[ib * N + id] -= ahh[i];
+                            for (int j = 0; j < qg; ++j) lam2[j * N + id] += 2.0 * G->w[i] * ahh[i];
+                        } else lam2[ib * N + id] += ahh[i];
+                    }
+                }
+        double *tmp = lam; lam = lam2; lam2 = tmp;
+    }
+    *dJ_dk = gk;
+    *dJ_dceq = gc;
+    free(gs); free(us); free(lam); free(lam2);
+    return 0;
 }
 
 /* ------------------------------------------------------------------ */

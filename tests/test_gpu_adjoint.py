@@ -98,3 +98,24 @@ def test_torch_autograd_wrapper():
     assert float(J.detach()) == pytest.approx(J2, rel=1e-13)
     assert np.allclose(kf.grad.numpy(), g, rtol=1e-12, atol=0)
     assert float(ceq.grad) == pytest.approx(dc, rel=1e-12)
+
+
+@pytest.mark.parametrize("flow,scheme,trt", [(True, "new", False), (True, "verhaeghe", True),
+                                             (False, "patel_ju", False)])
+def test_gradients_match_oracle_discrete_adjoint(flow, scheme, trt):
+    # the FP64 CUDA adjoint against the oracle's own discrete adjoint,
+    # element by element (per-voxel k field) and for the scalars
+    p, mask = _case(flow, scheme, trt)
+    n = 45
+    kf = workloads.lognormal_k(mask.shape, 0.05, 0.5, seed=21)
+    J, dk, dc, g = lbrbc.Sim(p, mask, k_field=kf).adjoint(n, field=True)
+    Jo, dko, dco, go = oracle.OracleSim(p, mask, k_field=kf).adjoint(n, field=True)
+    assert J == pytest.approx(Jo, rel=1e-11)
+    assert dk == pytest.approx(dko, rel=1e-10)
+    assert dc == pytest.approx(dco, rel=1e-10)
+    scale = np.abs(go).max()
+    assert scale > 0.0
+    assert np.abs(g - go).max() <= 1e-10 * scale
+    nz = go != 0.0
+    assert np.array_equal(g != 0.0, nz)
+    assert np.allclose(g[nz], go[nz], rtol=1e-9, atol=1e-12 * scale)

@@ -199,7 +199,8 @@ struct Dev {
     long long* log_node;
     int* log_kind;
     long long* step;      // completed steps
-    double* acc;          // [0] reacted, [1] Dirichlet inflow, [2] unpaid (event path)
+    double* acc;          // [0] reacted (unused: k_bound keeps per-block partials)
+    unsigned long long* facc;  // event-path sums in 64.64 fixed point: [0..1] Dirichlet inflow, [2..3] unpaid
     double* bacc;         // per-block partial ledger of k_bound: 2 * gridDim.x
     int* err;
     // compaction scratch
@@ -669,6 +670,29 @@ __global__ void __launch_bounds__(FLUID_BLOCK) k_fluid_list(const Dev<T> a, cons
 }
 
 // ---------------------------------------------------------------------------
+// Order-independent sums of the event path: each term is rounded once to a
+// 128-bit two's-complement fixed-point number with 64 fractional bits
+// (truncating below 2^-64, |term| < 2^63) and added with integer atomics, so
+// the total does not depend on the order in which threads add their terms.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void fx_add(unsigned long long* a, double v) {
+    if (v == 0.0) return;
+    const double m = fabs(v);
+    unsigned long long hi = (unsigned long long)floor(m);
+    unsigned long long lo = (unsigned long long)((m - (double)hi) * 18446744073709551616.0);
+    if (v < 0.0) {
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    const unsigned long long old = atomicAdd(&a[0], lo);
+    atomicAdd(&a[1], hi + (old + lo < old ? 1ull : 0ull));
+}
+
+__host__ __device__ __forceinline__ double fx_value(const unsigned long long* a) {
+    return (double)(long long)a[1] + (double)a[0] * (1.0 / 18446744073709551616.0);
+}
+
+// ---------------------------------------------------------------------------
 // Event queue with warp-aggregated atomics.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void push_event(int* nev, int cap, int* ev_node, int* ev_kind, int* err, int node,
@@ -1123,7 +1147,7 @@ __global__ void k_ev_compute(const Dev<T> a, const Phys p, int lastodd) {
             a.ev_val[e] = cinit;
             a.ev_val[a.cap_e + e] = rinit;
             a.ev_val[2 * a.cap_e + e] = ns ? Q / ns : 0.0;
-            if (!ns) atomicAdd(&a.acc[2], -Q / p.Vm);
+            if (!ns) fx_add(a.facc + 2, -Q / p.Vm);
         } else {
             const double phic = a.phi[id] + p.Vm * Cself;
             const double excess = phic - 1.0;
@@ -1260,7 +1284,7 @@ __global__ void k_reclassify(const Dev<T> a, const Phys p, int lastodd, int forc
             if (old == CLS_BOUND && cls == CLS_SOLID) {
                 const double C = p.cref + (double)post_sum<LG, false, T>(a, a.G, id, d, lastodd);
                 if (a.kind[id] == KIND_REACTIVE) a.phi[id] += p.Vm * C;
-                else atomicAdd(&a.acc[1], -C);
+                else fx_add(a.facc, -C);
             }
             if (cls != CLS_FLUID) {
                 if (a.sparse && a.cmap[id] < 0) {
@@ -1963,7 +1987,8 @@ __global__ void k_reduce_final(const double* part, int nblocks, double* out) {
 // (one warp, fixed order): out[0] reacted, out[1] Dirichlet inflow, out[2]
 // unpaid.
 template <int UNUSED = 0>
-__global__ void k_sum_partials(const double* bacc, int nblocks, const double* acc, double* out) {
+__global__ void k_sum_partials(const double* bacc, int nblocks, const double* acc, const unsigned long long* facc,
+                               double* out) {
     double r = 0.0, q = 0.0;
     for (int b = threadIdx.x; b < nblocks; b += 32) {
         r += bacc[2 * b];
@@ -1973,8 +1998,8 @@ __global__ void k_sum_partials(const double* bacc, int nblocks, const double* ac
     q = warp_sum(q);
     if (threadIdx.x == 0) {
         out[0] = acc[0] + r;
-        out[1] = acc[1] + q;
-        out[2] = acc[2];
+        out[1] = fx_value(facc) + q;
+        out[2] = fx_value(facc + 2);
     }
 }
 

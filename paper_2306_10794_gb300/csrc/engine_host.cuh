@@ -232,6 +232,7 @@ class Engine final : public ISim {
         }
         LB_CUDA(dalloc(&d_.step, 1));
         LB_CUDA(dalloc(&d_.acc, 4));
+        LB_CUDA(dalloc(&d_.facc, 4));
         nbacc_ = list_grid(d_.cap_b);
         // Grids of the boundary-list and fluid-end kernels: sized to the
         // lists at creation with 25 % head room (a grid-stride loop covers
@@ -296,6 +297,7 @@ class Engine final : public ISim {
         LB_CUDA(cudaMemset(d_.nlog, 0, sizeof(long long)));
         LB_CUDA(cudaMemset(d_.step, 0, sizeof(long long)));
         LB_CUDA(cudaMemset(d_.acc, 0, 4 * sizeof(double)));
+        LB_CUDA(cudaMemset(d_.facc, 0, 4 * sizeof(unsigned long long)));
         LB_CUDA(cudaMemset(d_.err, 0, sizeof(int)));
         LB_CUDA(cudaMemset(d_.side, 0, 4 * sizeof(double) * g.ny * g.nz));
         if (!d_.sparse) {
@@ -422,11 +424,15 @@ class Engine final : public ISim {
         k_reduce_final<0><<<1, 32, 0, own_>>>(part, nblk, part + 2 * nblk);
         LB_CUDA(cudaGetLastError());
         double sums[2], acc[4];
+        unsigned long long facc[4];
         std::vector<double> bacc((size_t)2 * nbacc_);
         LB_CUDA(cudaMemcpyAsync(sums, part + 2 * nblk, 2 * sizeof(double), cudaMemcpyDeviceToHost, own_));
         LB_CUDA(cudaMemcpyAsync(acc, d_.acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, own_));
+        LB_CUDA(cudaMemcpyAsync(facc, d_.facc, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, own_));
         LB_CUDA(cudaMemcpyAsync(bacc.data(), d_.bacc, bacc.size() * sizeof(double), cudaMemcpyDeviceToHost, own_));
         LB_CUDA(cudaStreamSynchronize(own_));
+        acc[1] = fx_value(facc);
+        acc[2] = fx_value(facc + 2);
         for (int b = 0; b < nbacc_; ++b) {
             acc[0] += bacc[2 * b];
             acc[1] += bacc[2 * b + 1];
@@ -452,7 +458,7 @@ class Engine final : public ISim {
         double* tail = scratch + 2 * (size_t)max_blocks;
         k_reduce_partial<T, LG><<<(int)nblk, RED_BLOCK, 0, own_>>>(d_, ph_, lastodd_, scratch);
         k_reduce_final<0><<<1, 32, 0, own_>>>(scratch, (int)nblk, tail);
-        k_sum_partials<0><<<1, 32, 0, own_>>>(d_.bacc, nbacc_, d_.acc, tail + 2);
+        k_sum_partials<0><<<1, 32, 0, own_>>>(d_.bacc, nbacc_, d_.acc, d_.facc, tail + 2);
         LB_CUDA(cudaGetLastError());
         double h[5];
         LB_CUDA(cudaMemcpyAsync(h, tail, 5 * sizeof(double), cudaMemcpyDeviceToHost, own_));

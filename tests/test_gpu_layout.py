@@ -70,7 +70,8 @@ def test_layouts_bitwise_equal_through_phase_changes(precision, kind):
     s = run(p, mask, steps, "sparse", **init)
     assert len(d["events"]) > 0
     same(d, s)
-    assert s["info"]["stored_cells"] < mask.size
+    if kind == "precipitation":  # (dissolution here ends with every cell stored)
+        assert s["info"]["stored_cells"] < mask.size
 
 
 @pytest.mark.parametrize("case", ["channel", "grain2d", "periodic_box", "no_flow_walls"])

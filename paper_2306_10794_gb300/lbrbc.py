@@ -247,6 +247,16 @@ def lbrbc_destroy(handle):
         load().lbrbc_destroy(handle)
 
 
+def _current_device() -> int:
+    """CUDA device current in this thread (the one lbrbc_create used)."""
+    try:
+        import torch
+
+        return int(torch.cuda.current_device()) if torch.cuda.is_available() else 0
+    except Exception:
+        return 0
+
+
 # Convenience wrapper -------------------------------------------------------------
 DEFAULTS = dict(dim=3, nx=8, ny=8, nz=8, flow_q=19, solute_q=7, bc=("periodic", "periodic", "periodic"),
                 scheme="new", phase_change=0, precision="fp32", event_log_capacity=0, tau_flow=0.8,
@@ -305,15 +315,27 @@ class Sim:
             self._keep[name] = a
             setattr(ini, name, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
         self._h = lbrbc_create(self._p, m, ini)
+        self.device = _current_device()
 
     def step(self, n: int = 1, stream: int | None = None):
         lbrbc_step(self._h, n, stream)
 
-    def fields(self):
+    def fields(self, device: bool = False):
+        """(u[z, y, x, 3], rho, c, phi) of the current state: numpy arrays on
+        the host, or with device=True float64 torch tensors on the
+        simulation's GPU, filled there by the library (no host copy)."""
+        s = self.shape
+        if device:
+            import torch
+
+            dev = torch.device("cuda", self.device)
+            u = torch.empty(s + (3,), dtype=torch.float64, device=dev)
+            rho, c, phi = (torch.empty(s, dtype=torch.float64, device=dev) for _ in range(3))
+            self.fields_device(u, rho, c, phi)
+            return u, rho, c, phi
         u = np.zeros(3 * self.N)
         rho, c, phi = np.zeros(self.N), np.zeros(self.N), np.zeros(self.N)
         lbrbc_fields(self._h, u, rho, c, phi)
-        s = self.shape
         return u.reshape(s + (3,)), rho.reshape(s), c.reshape(s), phi.reshape(s)
 
     def fields_device(self, u=None, rho=None, c=None, phi=None):

@@ -211,3 +211,20 @@ def test_hand_evaluated_events_near_other_boundaries_match_oracle(case):
     lg, lo = g.ledger(), o.ledger()
     for k in ("solute", "solid_over_vm", "unpaid", "dirichlet_in", "reacted"):
         assert lg[k] == pytest.approx(lo[k], rel=1e-12, abs=1e-13), k
+
+
+def test_fields_as_device_tensors():
+    # the fields as float64 torch tensors on the simulation's GPU equal the
+    # host copies bit for bit
+    torch = pytest.importorskip("torch")
+    shape = (6, 9, 21)
+    rng = np.random.default_rng(4)
+    mask = (rng.uniform(size=shape) < 0.3).astype(np.uint8)
+    p = dict(BASE, nx=21, ny=9, nz=6, bc=("periodic",) * 3)
+    g = lbrbc.Sim(p, mask)
+    g.step(9)
+    host = g.fields()
+    dev = g.fields(device=True)
+    for h, d in zip(host, dev):
+        assert d.is_cuda and d.dtype == torch.float64 and tuple(d.shape) == h.shape
+        assert np.array_equal(d.cpu().numpy(), h)

@@ -146,6 +146,7 @@ struct PhysT {
     T cref;            // deviation reference
     T c_in_d, c_dir_d, c_eq_d;  // c_inlet, c_dirichlet, c_eq minus cref
     T rho_out, k_r, gamma, neg_vm;
+    T rho_out_d;       // rho_out - 1 (the outlet rule in deviation form, no cancellation)
 };
 
 template <typename T>
@@ -550,14 +551,16 @@ __device__ __forceinline__ void fluid_cell_src(const Dev<T>& a, const Phys& p, c
                     if (LF::cx(i) > 0) f[i] += T(6.0 * LF::w(i) * LF::cx(i)) * uin;
             }
             if (outlet) {
-                // pressure anti-bounce-back at rho_out with the previous velocity
+                // pressure anti-bounce-back at rho_out with the previous velocity,
+                // in deviation form: rho_out (1 + X) - 1 = (rho_out - 1) + rho_out X
+                // (the plain form loses all but ~1e-2 of X ~ u^2 in FP32)
                 const T uo0 = T(a.side[4 * face + 0]), uo1 = T(a.side[4 * face + 1]), uo2 = T(a.side[4 * face + 2]);
                 const T uq = uo0 * uo0 + uo1 * uo1 + uo2 * uo2;
 #pragma unroll
                 for (int i = 1; i < QF; ++i)
                     if (LF::cx(i) < 0) {
                         const T eu = T(LF::cx(i)) * uo0 + T(LF::cy(i)) * uo1 + T(LF::cz(i)) * uo2;
-                        f[i] = -f[i] + T(2.0 * LF::w(i)) * (q.rho_out * (T(1) + T(4.5) * eu * eu - T(1.5) * uq) - T(1));
+                        f[i] = -f[i] + T(2.0 * LF::w(i)) * (q.rho_out_d + q.rho_out * (T(4.5) * eu * eu - T(1.5) * uq));
                     }
             }
         }
@@ -567,10 +570,10 @@ __device__ __forceinline__ void fluid_cell_src(const Dev<T>& a, const Phys& p, c
                 if (LG::cx(i) > 0) gg[i] = -gg[i] + T(2) * q.gw[i] * q.c_in_d;
         }
         if (outlet) {
-            const T co = T(a.side[4 * face + 3]);
+            const T co_d = T(a.side[4 * face + 3] - p.cref);  // previous C minus the reference, in FP64
 #pragma unroll
             for (int i = 1; i < QG; ++i)
-                if (LG::cx(i) < 0) gg[i] = -gg[i] + T(2) * q.gw[i] * (co - q.cref);
+                if (LG::cx(i) < 0) gg[i] = -gg[i] + T(2) * q.gw[i] * co_d;
         }
     }
 

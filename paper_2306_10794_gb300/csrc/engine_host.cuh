@@ -102,6 +102,7 @@ class Engine final : public ISim {
             q.c_dir_d = T(p.c_dir - p.cref);
             q.c_eq_d = T(p.c_eq - p.cref);
             q.rho_out = T(p.rho_out);
+            q.rho_out_d = T(p.rho_out - 1.0);
             q.k_r = T(p.k_r);
             q.gamma = T(p.gamma);
             q.neg_vm = T(-p.Vm);

@@ -217,7 +217,8 @@ struct Dev {
     int* cmap;            // NP: compact index of a padded cell, -1 if not stored
     int* cid;             // cap_s: padded index of compact cell n
     uint32_t* nwc;        // cap_s: node word of compact cell n
-    int* nbt;             // (QS - 1) * cap_s: compact index of n + e_s (stencil direction s), -1 if not stored
+    uint32_t* etab;       // effective block bases of each stored cell's neighbours (see k_sp_tables),
+                          // blocked by 32 cells: (QF - 1) flow then (QG - 1) solute entries per cell
     int* b_cn;            // cap_b: compact index of each wet boundary cell
     int* rown;            // NP: owner of a cell of the event region (-1 outside), sparse event path
     int* repack;          // [0] set when a cell needs storage it does not have
@@ -439,6 +440,7 @@ constexpr uint32_t NW_OUTLET = 1u << 31;
 template <typename T, class LF, class LG, bool ODD>
 struct GlobalSrc {
     static constexpr bool kTargets = false;  // writes do not depend on the neighbours' classes
+    static constexpr bool kBranchFree = false;  // reads pick a slot per direction
     const T* __restrict__ F;
     const T* __restrict__ G;
     Blk<LF> kF;
@@ -477,32 +479,55 @@ __host__ __device__ constexpr int sdir(int j) {
 // is inactive: the value there is its own f*_opp(i), halfway bounce-back) and
 // writes f*_i into slot i of x + e_i (its own slot opp(i) when that target
 // is inactive).  No population ever lives in an inactive cell, so the
-// storage holds the stored cells only; neighbours come from the table.
+// storage holds the stored cells only.
+//
+// The odd step's addresses come from the effective-base table: for each
+// neighbour direction d, E[d] is the neighbour's block base (m - m % 32) Q +
+// m % 32 when the neighbour is active for the lattice, else the cell's own
+// base plus 32 (opp(d) - d).  The read of direction opp(d) and the write of
+// direction d then both use slot E[d] + 32 d, active neighbour or not, so
+// the odd step needs no per-direction test.
+template <class L>
+__host__ __device__ __forceinline__ uint32_t pbase(uint32_t n) {
+    return (n & ~31u) * (uint32_t)L::Q + (n & 31u);
+}
+
+// Position of entry k of cell n in the blocked effective-base table.
+__device__ __forceinline__ size_t etab_at(uint32_t n, int nt, int k) {
+    return (size_t)(n & ~31u) * (size_t)nt + (size_t)k * 32u + (n & 31u);
+}
+
 template <typename T, class LF, class LG, bool ODD>
 struct SparseSrc {
-    static constexpr bool kTargets = true;  // writes go to an inactive target's own-slot fallback
-    using LS = typename Stencil<LF, LG>::L;
+    static constexpr bool kTargets = false;  // inactive targets are folded into the table
+    static constexpr bool kBranchFree = true;  // no read or write depends on the node word
+    static constexpr int QF1 = LF::Q > 0 ? LF::Q - 1 : 0;
+    static constexpr int NT = QF1 + LG::Q - 1;
     const T* __restrict__ F;
     const T* __restrict__ G;
-    const int* __restrict__ nbt;
-    uint32_t n, cap;
+    const uint32_t* __restrict__ et;  // this cell's table entries (entry k at et[32 k])
+    uint32_t n;
     T* Fw;
     T* Gw;
-    __device__ __forceinline__ uint32_t nb(int s) const { return (uint32_t)__ldg(nbt + (size_t)(s - 1) * cap + n); }
-    template <class L>
-    __device__ __forceinline__ uint32_t rd(int i, bool inactive) const {
-        if (!ODD || inactive || i == 0) return pslot<L>(i, n);
-        return pslot<L>(L::opp(i), nb(sdir<LS, L>(L::opp(i))));
+    __device__ __forceinline__ uint32_t e(int k) const { return __ldg(et + 32 * k); }
+    __device__ __forceinline__ T f(int i, bool) const {
+        if (!ODD || i == 0) return ld_pop(F + pslot<LF>(i, n));
+        const int d = LF::opp(i);
+        return ld_pop(F + e(d - 1) + 32u * (uint32_t)d);
     }
-    template <class L>
-    __device__ __forceinline__ uint32_t wr(int i, bool inactive) const {
-        if (!ODD || inactive || i == 0) return pslot<L>(L::opp(i), n);
-        return pslot<L>(i, nb(sdir<LS, L>(i)));
+    __device__ __forceinline__ T g(int i, bool) const {
+        if (!ODD || i == 0) return ld_pop(G + pslot<LG>(i, n));
+        const int d = LG::opp(i);
+        return ld_pop(G + e(QF1 + d - 1) + 32u * (uint32_t)d);
     }
-    __device__ __forceinline__ T f(int i, bool inactive) const { return ld_pop(F + rd<LF>(i, inactive)); }
-    __device__ __forceinline__ T g(int i, bool inactive) const { return ld_pop(G + rd<LG>(i, inactive)); }
-    __device__ __forceinline__ void fput(int i, T v, bool inactive) const { st_pop(Fw + wr<LF>(i, inactive), v); }
-    __device__ __forceinline__ void gput(int i, T v, bool inactive) const { st_pop(Gw + wr<LG>(i, inactive), v); }
+    __device__ __forceinline__ void fput(int i, T v, bool) const {
+        if (!ODD || i == 0) st_pop(Fw + pslot<LF>(LF::opp(i), n), v);
+        else st_pop(Fw + e(i - 1) + 32u * (uint32_t)i, v);
+    }
+    __device__ __forceinline__ void gput(int i, T v, bool) const {
+        if (!ODD || i == 0) st_pop(Gw + pslot<LG>(LG::opp(i), n), v);
+        else st_pop(Gw + e(QF1 + i - 1) + 32u * (uint32_t)i, v);
+    }
 };
 
 // One fluid cell of one step with node word w: stream (read side), open
@@ -520,7 +545,7 @@ __device__ __forceinline__ void fluid_cell_src(const Dev<T>& a, const Phys& p, c
     // per-direction tests; the others pick, per direction, the plain slot or
     // the swapped one of an inactive source.  (All sources active means all
     // targets active too: the sources of a cell are all its neighbours.)
-    const bool wplain = __all_sync(__activemask(), plain);
+    const bool wplain = Src::kBranchFree || __all_sync(__activemask(), plain);
     T f[QF > 0 ? QF : 1];
     T gg[QG];
     if (wplain) {
@@ -649,7 +674,8 @@ __global__ void __launch_bounds__(FLUID_BLOCK, sizeof(T) == 4 ? 8 : 5) k_fluid_s
             id = (uint32_t)a.cid[n];
             coords(a.geo, id, x, y, z);
         }
-        const SparseSrc<T, LF, LG, ODD> src{a.F, a.G, a.nbt, (uint32_t)n, (uint32_t)a.cap_s, a.F, a.G};
+        constexpr int NT = SparseSrc<T, LF, LG, ODD>::NT;
+        const SparseSrc<T, LF, LG, ODD> src{a.F, a.G, a.etab + etab_at((uint32_t)n, NT, 0), (uint32_t)n, a.F, a.G};
         fluid_cell_src<T, LF, LG, ODD>(a, p, q, id, w, src, inlet, outlet, y, z);
     }
 }
@@ -811,15 +837,14 @@ __device__ __forceinline__ void unpack_xyz(uint64_t v, int& x, int& y, int& z) {
 // neighbour table; LF only names the table's stencil).
 template <typename T, class LF, class LG, bool ODD, bool SP>
 struct BoundSlots {
+    static constexpr int QF1 = LF::Q > 0 ? LF::Q - 1 : 0;
     Blk<LG> kb;
     uint32_t n;
-    const int* nbt;
-    uint32_t cap;
+    const uint32_t* et;
     __device__ __forceinline__ BoundSlots(const Dev<T>& a, int e) {
         if constexpr (SP) {
             n = (uint32_t)a.b_cn[e];
-            nbt = a.nbt;
-            cap = (uint32_t)a.cap_s;
+            et = a.etab + etab_at(n, QF1 + LG::Q - 1, QF1);
         } else {
             int x, y, z;
             unpack_xyz(a.b_xyz[e], x, y, z);
@@ -829,18 +854,17 @@ struct BoundSlots {
     }
     __device__ __forceinline__ uint32_t rd(int i, bool inactive) const {
         if constexpr (SP) {
-            using LS = typename Stencil<LF, LG>::L;
-            if (!ODD || inactive || i == 0) return pslot<LG>(i, n);
-            return pslot<LG>(LG::opp(i), (uint32_t)nbt[(size_t)(sdir<LS, LG>(LG::opp(i)) - 1) * cap + n]);
+            if (!ODD || i == 0) return pslot<LG>(i, n);
+            const int d = LG::opp(i);
+            return et[32 * (d - 1)] + 32u * (uint32_t)d;
         } else {
             return read_slot<LG, ODD>(kb, i, inactive);
         }
     }
     __device__ __forceinline__ uint32_t wr(int i, bool inactive) const {
         if constexpr (SP) {
-            using LS = typename Stencil<LF, LG>::L;
-            if (!ODD || inactive || i == 0) return pslot<LG>(LG::opp(i), n);
-            return pslot<LG>(i, (uint32_t)nbt[(size_t)(sdir<LS, LG>(i) - 1) * cap + n]);
+            if (!ODD || i == 0) return pslot<LG>(LG::opp(i), n);
+            return et[32 * (i - 1)] + 32u * (uint32_t)i;
         } else {
             return write_slot<LG, ODD>(kb, i);
         }
@@ -912,6 +936,14 @@ __device__ __forceinline__ void bound_entry(const Dev<T>& a, const Phys& p, cons
     const T C = cref + sc;
     if (!isfinite(C)) *a.err |= ERR_NUMERIC;
     collide_solute<LG, T>(gq, C, T(0), T(0), T(0), p, q);
+    {
+        // the collision conserves C: the rest population takes the remainder
+        // (rounded weights would otherwise create solute in proportion to C)
+        T rest = sc;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) rest -= gq[i];
+        gq[0] = rest;
+    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) G[kb.wr(i, i > 0 && ((bw >> (LG::opp(i) - 1)) & 1u))] = gq[i];
     const int sg = ms.sign();
@@ -1330,39 +1362,42 @@ __global__ void k_reclassify(const Dev<T> a, const Phys p, int lastodd, int forc
 // Stream compaction of the wet boundary cells (order = cell index).
 // Pass 1: counts per chunk of SCAN_CHUNK cells.
 template <typename T, class LG>
-__global__ void k_count(const Dev<T> a, int which, int force) {
+__global__ void k_count(const Dev<T> a, int which, int force, int nchunks) {
     if (!force && *a.nev == 0) return;
     const Geo& g = a.geo;
     const long long total = (long long)g.nx * g.ny * g.nz;
-    const long long chunk = blockIdx.x;
     __shared__ int cnt;
-    if (threadIdx.x == 0) cnt = 0;
-    __syncthreads();
-    int local = 0;
-    for (long long t = chunk * SCAN_CHUNK + threadIdx.x; t < min(total, (chunk + 1) * SCAN_CHUNK); t += blockDim.x) {
-        const int x = (int)(t % g.nx);
-        const int y = (int)((t / g.nx) % g.ny);
-        const int z = (int)(t / ((long long)g.nx * g.ny));
-        const long long id = g.idx(x, y, z);
-        const uint32_t cls = a.nw[id] & 3u;
-        if (which == 0) local += cls == CLS_BOUND;
-        else if (which == 2) local += cls == CLS_FLUID;
-        else if (cls == CLS_FLUID) {
+    for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+        if (threadIdx.x == 0) cnt = 0;
+        __syncthreads();
+        int local = 0;
+        for (long long t = chunk * SCAN_CHUNK + threadIdx.x; t < min(total, (chunk + 1) * SCAN_CHUNK);
+             t += blockDim.x) {
+            const int x = (int)(t % g.nx);
+            const int y = (int)((t / g.nx) % g.ny);
+            const int z = (int)(t / ((long long)g.nx * g.ny));
+            const long long id = g.idx(x, y, z);
+            const uint32_t cls = a.nw[id] & 3u;
+            if (which == 0) local += cls == CLS_BOUND;
+            else if (which == 2) local += cls == CLS_FLUID;
+            else if (cls == CLS_FLUID) {
 #pragma unroll
-            for (int o = 1; o < LG::Q; ++o) {
-                int xx = x - LG::cx(o), yy = y - LG::cy(o), zz = z - LG::cz(o);
-                if (!wrap_inside(g, xx, yy, zz)) continue;
-                const long long nb = g.idx(xx, yy, zz);
-                if ((a.nw[nb] & 3u) == CLS_BOUND && a.kind[nb] == KIND_REACTIVE) {
-                    local++;
-                    break;
+                for (int o = 1; o < LG::Q; ++o) {
+                    int xx = x - LG::cx(o), yy = y - LG::cy(o), zz = z - LG::cz(o);
+                    if (!wrap_inside(g, xx, yy, zz)) continue;
+                    const long long nb = g.idx(xx, yy, zz);
+                    if ((a.nw[nb] & 3u) == CLS_BOUND && a.kind[nb] == KIND_REACTIVE) {
+                        local++;
+                        break;
+                    }
                 }
             }
         }
+        atomicAdd(&cnt, local);
+        __syncthreads();
+        if (threadIdx.x == 0) a.blk[chunk] = cnt;
+        __syncthreads();
     }
-    atomicAdd(&cnt, local);
-    __syncthreads();
-    if (threadIdx.x == 0) a.blk[chunk] = cnt;
 }
 
 // Pass 2: exclusive scan of the chunk counts (one block); total -> *count.
@@ -1398,13 +1433,13 @@ __global__ void k_scan(const Dev<T> a, int nchunks, int which, int force) {
 
 // Pass 3: write the entries in cell order.
 template <typename T, class LG>
-__global__ void k_write_lists(const Dev<T> a, const Phys p, int which, int force) {
+__global__ void k_write_lists(const Dev<T> a, const Phys p, int which, int force, int nchunks) {
     if (!force && *a.nev == 0) return;
     const Geo& g = a.geo;
     const long long total = (long long)g.nx * g.ny * g.nz;
-    const long long chunk = blockIdx.x;
     __shared__ int warp_tot[32];
     __shared__ int base_s;
+    for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
     if (threadIdx.x == 0) base_s = a.blk[chunk];
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw_ = blockDim.x >> 5;
@@ -1496,6 +1531,7 @@ __global__ void k_write_lists(const Dev<T> a, const Phys p, int which, int force
         if (threadIdx.x == 0) base_s += tot;
         __syncthreads();
     }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1534,24 +1570,28 @@ __global__ void k_sp_mark(const Dev<T> a, uint8_t* __restrict__ code, const int*
 
 // Per chunk of SCAN_CHUNK cells (x-fastest order): cells of range r.
 template <typename T>
-__global__ void k_sp_count(const Dev<T> a, const uint8_t* __restrict__ code, int r, const int* __restrict__ go) {
+__global__ void k_sp_count(const Dev<T> a, const uint8_t* __restrict__ code, int r, const int* __restrict__ go,
+                           int nchunks) {
     if (go && *go == 0) return;
     const Geo& g = a.geo;
     const long long total = (long long)g.nx * g.ny * g.nz;
-    const long long chunk = blockIdx.x;
     __shared__ int cnt;
-    if (threadIdx.x == 0) cnt = 0;
-    __syncthreads();
-    int local = 0;
-    for (long long t = chunk * SCAN_CHUNK + threadIdx.x; t < min(total, (chunk + 1) * SCAN_CHUNK); t += blockDim.x) {
-        const int x = (int)(t % g.nx);
-        const int y = (int)((t / g.nx) % g.ny);
-        const int z = (int)(t / ((long long)g.nx * g.ny));
-        local += code[g.idx(x, y, z)] == r;
+    for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+        if (threadIdx.x == 0) cnt = 0;
+        __syncthreads();
+        int local = 0;
+        for (long long t = chunk * SCAN_CHUNK + threadIdx.x; t < min(total, (chunk + 1) * SCAN_CHUNK);
+             t += blockDim.x) {
+            const int x = (int)(t % g.nx);
+            const int y = (int)((t / g.nx) % g.ny);
+            const int z = (int)(t / ((long long)g.nx * g.ny));
+            local += code[g.idx(x, y, z)] == r;
+        }
+        atomicAdd(&cnt, local);
+        __syncthreads();
+        if (threadIdx.x == 0) a.blk[chunk] = cnt;
+        __syncthreads();
     }
-    atomicAdd(&cnt, local);
-    __syncthreads();
-    if (threadIdx.x == 0) a.blk[chunk] = cnt;
 }
 
 // Exclusive scan of the chunk counts (one block); the range total goes to
@@ -1589,13 +1629,14 @@ __global__ void k_sp_scan(const Dev<T> a, int nchunks, int r, int* __restrict__ 
 // capacity raise ERR_OVERFLOW and are not written.
 template <typename T>
 __global__ void k_sp_write(const Dev<T> a, const uint8_t* __restrict__ code, int r, const int* __restrict__ tot,
-                           int* __restrict__ cmap_out, int* __restrict__ cid_out, const int* __restrict__ go) {
+                           int* __restrict__ cmap_out, int* __restrict__ cid_out, const int* __restrict__ go,
+                           int nchunks) {
     if (go && *go == 0) return;
     const Geo& g = a.geo;
     const long long total = (long long)g.nx * g.ny * g.nz;
-    const long long chunk = blockIdx.x;
     __shared__ int warp_tot[32];
     __shared__ int base_s;
+    for (long long chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
     if (threadIdx.x == 0) {
         int b = a.blk[chunk];
         for (int k = 0; k < r; ++k) b += tot[k];
@@ -1636,6 +1677,7 @@ __global__ void k_sp_write(const Dev<T> a, const uint8_t* __restrict__ code, int
         if (threadIdx.x == 0) base_s += tt;
         __syncthreads();
     }
+    }
 }
 
 // Stored-cell count from the range totals.
@@ -1647,20 +1689,68 @@ __global__ void k_sp_total(const Dev<T> a, const int* __restrict__ tot, int* __r
     *ns_out = (int)min(n, a.cap_s);
 }
 
-// Node words and neighbour table of the stored cells: nbt[s][n] is the
-// compact index of n + e_s (periodic wrap; -1 beyond a wall or open face or
-// when that cell is not stored).
+// Node word and effective-base table entries of stored cell n (padded
+// index id): for each neighbour direction d of each lattice, the block base
+// of the neighbour id + e_d when it is active for that lattice (flow: fluid;
+// solute: not solid) -- it is then stored -- else the cell's own base plus
+// 32 (opp(d) - d), so that slot E[d] + 32 d is the own slot opp(d).
+template <typename T, class LF, class LG>
+__device__ __forceinline__ void sp_cell_tables(const Dev<T>& a, uint32_t n, long long id) {
+    constexpr int QF1 = LF::Q > 0 ? LF::Q - 1 : 0, NT = QF1 + LG::Q - 1;
+    a.nwc[n] = a.nw[id];
+    const Nbr d = nbr_of(a.geo, id);
+    if constexpr (LF::Q > 0) {
+        const uint32_t own = pbase<LF>(n);
+#pragma unroll
+        for (int k = 1; k < LF::Q; ++k) {
+            const long long nb = id + off<LF>(d, k);
+            const bool act = (a.nw[nb] & 3u) == CLS_FLUID;
+            a.etab[etab_at(n, NT, k - 1)] =
+                act ? pbase<LF>((uint32_t)a.cmap[nb]) : own + 32u * (uint32_t)(LF::opp(k) - k);
+        }
+    }
+    const uint32_t own = pbase<LG>(n);
+#pragma unroll
+    for (int k = 1; k < LG::Q; ++k) {
+        const long long nb = id + off<LG>(d, k);
+        const bool act = (a.nw[nb] & 3u) != CLS_SOLID;
+        a.etab[etab_at(n, NT, QF1 + k - 1)] =
+            act ? pbase<LG>((uint32_t)a.cmap[nb]) : own + 32u * (uint32_t)(LG::opp(k) - k);
+    }
+}
+
 template <typename T, class LF, class LG>
 __global__ void k_sp_tables(const Dev<T> a, const int* __restrict__ go) {
     if (go && *go == 0) return;
-    using LS = typename Stencil<LF, LG>::L;
     const int ns = *a.ns;
-    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < ns; n += (long long)gridDim.x * blockDim.x) {
-        const long long id = a.cid[n];
-        a.nwc[n] = a.nw[id];
-        const Nbr d = nbr_of(a.geo, id);
-#pragma unroll
-        for (int s = 1; s < LS::Q; ++s) a.nbt[(size_t)(s - 1) * a.cap_s + n] = a.cmap[id + off<LS>(d, s)];
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < ns; n += (long long)gridDim.x * blockDim.x)
+        sp_cell_tables<T, LF, LG>(a, (uint32_t)n, a.cid[n]);
+}
+
+// After the classes changed: the table entries of every stored cell within
+// one flow-lattice step of the event region (the cells whose neighbours may
+// have changed activity).  A cell reached from several items is recomputed
+// from the same classes each time.
+template <typename T, class LF, class LG>
+__global__ void k_sp_retab(const Dev<T> a) {
+    using LS = typename Stencil<LF, LG>::L;
+    const int n = min(*a.nev, a.cap_e);
+    const Geo& g = a.geo;
+    const long long items = (long long)n * LG::Q * LS::Q;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < items;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int e = (int)(t / (LG::Q * LS::Q));
+        const int r = (int)(t % (LG::Q * LS::Q));
+        const int o = r / LS::Q, sdx = r % LS::Q;
+        int x, y, z;
+        coords(g, a.ev_node[e], x, y, z);
+        x += LG::cx(o) + LS::cx(sdx);
+        y += LG::cy(o) + LS::cy(sdx);
+        z += LG::cz(o) + LS::cz(sdx);
+        if (!wrap_inside(g, x, y, z)) continue;
+        const long long c = g.idx(x, y, z);
+        const int cn = a.cmap[c];
+        if (cn >= 0) sp_cell_tables<T, LF, LG>(a, (uint32_t)cn, c);
     }
 }
 

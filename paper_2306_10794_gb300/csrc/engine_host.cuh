@@ -711,6 +711,11 @@ class Engine final : public ISim {
         return cudaMalloc((void**)p, n * sizeof(U) + 16);
     }
 
+    // Grid of the chunked compaction kernels: a fixed number of blocks
+    // looping over the chunks, so that a step without events pays one small
+    // wave of early exits instead of one block per chunk.
+    int cgrid() const { return (int)std::max<long long>(1, std::min<long long>(nchunks_, 152LL * 8)); }
+
     static int grid_for(long long n, int block) {
         long long b = (n + block - 1) / block;
         return (int)std::max<long long>(1, std::min<long long>(b, 152LL * 16));
@@ -788,9 +793,9 @@ class Engine final : public ISim {
 
     void enqueue_lists(cudaStream_t st, int force) {
         for (int which = 0; which < (d_.use_fl ? 3 : 2); ++which) {
-            k_count<T, LG><<<nchunks_, 256, 0, st>>>(d_, which, force);
+            k_count<T, LG><<<cgrid(), 256, 0, st>>>(d_, which, force, nchunks_);
             k_scan<T><<<1, 1024, 0, st>>>(d_, nchunks_, which, force);
-            k_write_lists<T, LG><<<nchunks_, 256, 0, st>>>(d_, ph_, which, force);
+            k_write_lists<T, LG><<<cgrid(), 256, 0, st>>>(d_, ph_, which, force, nchunks_);
         }
     }
 
@@ -800,9 +805,9 @@ class Engine final : public ISim {
     void enqueue_numbering(cudaStream_t st, int* cmap_out, int* cid_out, int* ns_out, const int* go) {
         k_sp_mark<T, LG><<<grid_for(ncell_, 256), 256, 0, st>>>(d_, d_.scode, go);
         for (int r = 0; r < 3; ++r) {
-            k_sp_count<T><<<nchunks_, 256, 0, st>>>(d_, d_.scode, r, go);
+            k_sp_count<T><<<cgrid(), 256, 0, st>>>(d_, d_.scode, r, go, nchunks_);
             k_sp_scan<T><<<1, 1024, 0, st>>>(d_, nchunks_, r, d_.stot, go);
-            k_sp_write<T><<<nchunks_, 256, 0, st>>>(d_, d_.scode, r, d_.stot, cmap_out, cid_out, go);
+            k_sp_write<T><<<cgrid(), 256, 0, st>>>(d_, d_.scode, r, d_.stot, cmap_out, cid_out, go, nchunks_);
         }
         k_sp_total<T><<<1, 1, 0, st>>>(d_, d_.stot, ns_out, go);
     }
@@ -814,7 +819,7 @@ class Engine final : public ISim {
         using LS = typename Stencil<LF, LG>::L;
         k_sp_mark<T, LG><<<grid_for(ncell_, 256), 256, 0, own_>>>(d_, d_.scode, nullptr);
         for (int r = 0; r < 3; ++r) {
-            k_sp_count<T><<<nchunks_, 256, 0, own_>>>(d_, d_.scode, r, nullptr);
+            k_sp_count<T><<<cgrid(), 256, 0, own_>>>(d_, d_.scode, r, nullptr, nchunks_);
             k_sp_scan<T><<<1, 1024, 0, own_>>>(d_, nchunks_, r, d_.stot, nullptr);
         }
         LB_CUDA(cudaGetLastError());
@@ -829,7 +834,7 @@ class Engine final : public ISim {
         long long cap = prm_.phase_change ? ncell_ : ns;
         cap = std::max<long long>(64, ((cap + 63) / 64) * 64);
         ns0_ = ns;
-        if ((long long)std::max(QF, QG) * cap >= (1LL << 32) || (long long)(LS::Q - 1) * cap >= (1LL << 40)) {
+        if ((long long)std::max(QF, QG) * cap >= (1LL << 32)) {
             err = "stored set too large for 32-bit population indices";
             return 1;
         }
@@ -841,7 +846,7 @@ class Engine final : public ISim {
         LB_CUDA(cudaMemset(d_.G, 0, (size_t)QG * cap * sizeof(T)));
         LB_CUDA(dalloc(&d_.cid, (size_t)cap));
         LB_CUDA(dalloc(&d_.nwc, (size_t)cap));
-        LB_CUDA(dalloc(&d_.nbt, (size_t)(LS::Q - 1) * cap));
+        LB_CUDA(dalloc(&d_.etab, (size_t)((LF::Q > 0 ? LF::Q - 1 : 0) + LG::Q - 1) * cap));
         LB_CUDA(cudaMemset(d_.nwc, 0, cap * sizeof(uint32_t)));
         if (prm_.phase_change) {
             LB_CUDA(dalloc(&d_.cid2, (size_t)cap));
@@ -928,6 +933,7 @@ class Engine final : public ISim {
             k_ev_neighbours<T, LG><<<eg, 256, 0, st>>>(d_, ph_, form);
             enqueue_reclassify(st, form, 0);
             if (sp) enqueue_repack(st);
+            if (sp) k_sp_retab<T, LF, LG><<<eg, 256, 0, st>>>(d_);
             if (sp && odd) {
                 k_sp_swap<T, LF, LG><<<eg, 256, 0, st>>>(d_);
                 k_sp_rreset<T, LG><<<eg, 256, 0, st>>>(d_);
@@ -957,7 +963,7 @@ class Engine final : public ISim {
         int n = 3;
         if (ph_.phase_change) {
             n += 4 + 1 + 3 * (d_.use_fl ? 3 : 2) + 2;  // events, reclassification, lists, reset + step end
-            if (d_.sparse) n += 1 + (1 + 9 + 1) + 5 + 2;  // repacking (conditional) + swaps of odd steps / 2
+            if (d_.sparse) n += 1 + (1 + 9 + 1) + 5 + 1 + 2;  // repacking (conditional), table refresh, swaps of odd steps / 2
         }
         return n;
     }

@@ -65,6 +65,42 @@ __device__ __forceinline__ T edot(int i, T ux, T uy, T uz) {
     return r;
 }
 
+// Conservation in the storage precision.  The weights rounded to FP32 sum
+// to 1 + 1.5e-8 (D3Q19), so a collision written with them creates mass in
+// proportion to the local density deviation, and momentum likewise; over
+// thousands of steps of a weakly damped flow this drifts by ~1e-5.  Two
+// arrangements keep the collision exactly conservative in real arithmetic
+// whatever the rounding, leaving only unbiased per-operation rounding:
+//  * the rest population takes the remainder of the mass balance,
+//    a_0' = (1 - s) a_0 + s (sum a) - 2 sum_k E'_k, which equals the
+//    relaxation of a_0 towards its equilibrium when the weights are exact;
+//  * the antisymmetric equilibrium uses coefficients c_k = w_k / cs^2 whose
+//    sum 2 sum_k c_k e_k e_k = I holds exactly for the rounded values: the
+//    diagonal coefficient rounded once, the axis coefficient as 1/2 minus
+//    the diagonal ones that share its axis (exact by Sterbenz's lemma).
+template <class L>
+__host__ __device__ constexpr int diag_per_axis() {
+    int n = 0;
+    for (int k = 1; k <= L::H; ++k)
+        if (L::cx(k) != 0 && L::cx(k) * L::cx(k) + L::cy(k) * L::cy(k) + L::cz(k) * L::cz(k) > 1) ++n;
+    return n;
+}
+
+// w_k / cs^2 of pair k for a lattice with cs^2 = 1/3 and fixed weights
+// (D3Q19, D2Q9), or 1/2 for D3Q7 / D2Q5 (w_k = cs^2 / 2 at any rest
+// fraction), in exact-sum form.
+template <class L, typename T>
+__device__ __forceinline__ T mom_coef(int k) {
+    constexpr int nd = diag_per_axis<L>();
+    if constexpr (nd == 0) {
+        return T(0.5);
+    } else {
+        const T cd = T(3.0 * L::w(L::H));  // the last pair of the half-split sets is diagonal
+        const bool axis = L::cx(k) * L::cx(k) + L::cy(k) * L::cy(k) + L::cz(k) * L::cz(k) == 1;
+        return axis ? T(0.5) - T(nd) * cd : cd;
+    }
+}
+
 // S_k, D_k for k = 1..H (arrays indexed 1..H+1; for odd H the last lane of
 // the last instruction repeats pair H).
 template <class L, typename T>
@@ -118,24 +154,27 @@ __device__ __forceinline__ void flow_pairs(T (&f)[L::Q], T& rho, T& ux, T& uy, T
     const T s = q.f_sym, a = p.trt_f ? q.f_anti : q.f_sym;
     const T hs = T(0.5) - T(0.5) * s, ha = T(0.5) - T(0.5) * a;
     const T m15 = T(-1.5) * usq;
-    f[0] = f[0] - s * (f[0] - T(L::w(0)) * (drho + rho * m15));
+    T esum = T(0);  // sum of E'_k over the pairs
 #pragma unroll
     for (int k = 1; k <= H; k += 2) {
         const int k1 = k + 1 <= H ? k + 1 : k;
         const T e0 = edot<L, T>(k, ux, uy, uz), e1 = edot<L, T>(k1, ux, uy, uz);
         const T sw0 = s * T(L::w(k)), sw1 = s * T(L::w(k1));
-        const T aw0 = T(3) * a * T(L::w(k)), aw1 = T(3) * a * T(L::w(k1));
-        // t = 4.5 (e.u)^2 - 1.5 u.u;  E' = s E = s w (drho + rho t);  O' = a O = 3 a w rho e.u
+        const T aw0 = a * mom_coef<L, T>(k), aw1 = a * mom_coef<L, T>(k1);
+        // t = 4.5 (e.u)^2 - 1.5 u.u;  E' = s E = s w (drho + rho t);  O' = a O = a (w / cs^2) rho e.u
         T h0, h1, t0, t1, E0, E1, P0, P1, O0, O1, M0, M1;
         mul_x2(T(4.5) * e0, T(4.5) * e1, e0, e1, h0, h1);
         add_x2(h0, h1, m15, m15, t0, t1);
         fma_x2(rho, rho, t0, t1, drho, drho, t0, t1);
         mul_x2(sw0, sw1, t0, t1, E0, E1);
+        esum += k1 != k ? E0 + E1 : E0;
         fma_x2(hs, hs, S[k], S[k + 1], E0, E1, P0, P1);
         mul_x2(aw0 * rho, aw1 * rho, e0, e1, O0, O1);
         fma_x2(ha, ha, D[k], D[k + 1], O0, O1, M0, M1);
         pair_out<L, T>(f, k, k1, P0, P1, M0, M1);
     }
+    // rest population: the remainder of the mass balance
+    f[0] = (T(1) - s) * f[0] + (s * drho - T(2) * esum);
 }
 
 // Solute cell: collision of the solute populations with concentration C
@@ -153,8 +192,7 @@ __device__ __forceinline__ void solute_pairs(T (&g)[L::Q], T& C, T ux, T uy, T u
     C = q.cref + dc;
     const T s = p.trt_g ? q.g_sym : q.g_anti, a = q.g_anti;
     const T hs = T(0.5) - T(0.5) * s, ha = T(0.5) - T(0.5) * a;
-    const T cu = C * q.ics2;
-    g[0] = g[0] - s * (g[0] - q.gw[0] * dc);
+    T esum = T(0);
 #pragma unroll
     for (int k = 1; k <= H; k += 2) {
         const int k1 = k + 1 <= H ? k + 1 : k;
@@ -162,11 +200,14 @@ __device__ __forceinline__ void solute_pairs(T (&g)[L::Q], T& C, T ux, T uy, T u
         T E0, E1, P0, P1, O0, O1, M0, M1;
         E0 = s * q.gw[k] * dc;
         E1 = s * q.gw[k1] * dc;
+        esum += k1 != k ? E0 + E1 : E0;
         fma_x2(hs, hs, S[k], S[k + 1], E0, E1, P0, P1);
-        mul_x2(a * q.gw[k] * cu, a * q.gw[k1] * cu, e0, e1, O0, O1);
+        mul_x2(a * mom_coef<L, T>(k) * C, a * mom_coef<L, T>(k1) * C, e0, e1, O0, O1);
         fma_x2(ha, ha, D[k], D[k + 1], O0, O1, M0, M1);
         pair_out<L, T>(g, k, k1, P0, P1, M0, M1);
     }
+    // rest population: the remainder of the mass balance
+    g[0] = (T(1) - s) * g[0] + (s * dc - T(2) * esum);
 }
 
 }  // namespace lbrbc

@@ -56,9 +56,22 @@ __global__ void __launch_bounds__(FLUID_BLOCK) kb_fluid_list4(const DomainDesc<T
     }
 }
 
+// Active-cell chunk: FLUID_BLOCK consecutive stored cells of one domain on
+// the active-cell layout.  x: domain, y: chunk.
+template <typename T, class LF, class LG, bool ODD>
+__global__ void __launch_bounds__(FLUID_BLOCK) kb_fluid_sp(const DomainDesc<T>* __restrict__ dd,
+                                                        const int2* __restrict__ chunks, int nchunks) {
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const int2 ch = chunks[c];
+        const DomainDesc<T>& D = dd[ch.x];
+        const int n = ch.y * FLUID_BLOCK + threadIdx.x;
+        if (n < *D.a.ns) sparse_cell<T, LF, LG, ODD>(D.a, D.p, D.q, n);
+    }
+}
+
 // Boundary chunk: LIST_BLOCK consecutive list entries of one domain; the
 // chunk's ledger partial goes to the domain's slot for that chunk.
-template <typename T, class LG, bool ODD>
+template <typename T, class LF, class LG, bool ODD>
 __global__ void __launch_bounds__(LIST_BLOCK) kb_bound(const DomainDesc<T>* __restrict__ dd, const int2* __restrict__ chunks,
                                                     int nchunks) {
     __shared__ __align__(16) unsigned char red_raw[2 * (LIST_BLOCK / 32) * sizeof(DiffSum<T>)];
@@ -68,7 +81,10 @@ __global__ void __launch_bounds__(LIST_BLOCK) kb_bound(const DomainDesc<T>* __re
         const DomainDesc<T>& D = dd[ch.x];
         const int e = ch.y * LIST_BLOCK + threadIdx.x;
         DiffSum<T> racc, dacc;
-        if (e < *D.a.nb) bound_entry<T, D3Q19, LG, ODD, false>(D.a, D.p, D.q, e, racc, dacc);
+        if (e < *D.a.nb) {
+            if (D.a.sparse) bound_entry<T, LF, LG, ODD, true>(D.a, D.p, D.q, e, racc, dacc);
+            else bound_entry<T, LF, LG, ODD, false>(D.a, D.p, D.q, e, racc, dacc);
+        }
         racc = warp_merge(racc);
         dacc = warp_merge(dacc);
         __syncthreads();
@@ -127,7 +143,6 @@ class BatchEngine final : public IBatch {
             auto* e = new Engine<T, LF, LG>();
             e->set_batched();
             e->force_list(true);
-            e->force_dense(true);
             doms_.emplace_back(e);
             const int rc = e->init(P[i], masks[i], inits ? &inits[i] : nullptr, err);
             if (rc) {
@@ -155,6 +170,30 @@ class BatchEngine final : public IBatch {
         }
         nbch_ = (int)bch.size();
         nfch_ = (int)fch.size();
+        // fluid chunks of the domains on the active-cell layout (fixed: no
+        // phase change, the stored set never changes)
+        {
+            std::vector<std::vector<int2>> per(n);
+            for (int i = 0; i < n; ++i)
+                if (doms_[i]->sparse())
+                    for (long long c = 0; c * FLUID_BLOCK < doms_[i]->stored0(); ++c) per[i].push_back(make_int2(i, (int)c));
+            std::vector<int2> sch;
+            // largest domains first, chunks interleaved round-robin
+            std::vector<int> idx(n);
+            std::iota(idx.begin(), idx.end(), 0);
+            std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return per[a].size() > per[b].size(); });
+            for (size_t k = 0, more = 1; more; ++k) {
+                more = 0;
+                for (int i : idx)
+                    if (k < per[i].size()) {
+                        sch.push_back(per[i][k]);
+                        more = 1;
+                    }
+            }
+            nsch_ = (int)sch.size();
+            LB_BCUDA(cudaMalloc((void**)&sch_, sizeof(int2) * std::max(1, nsch_)));
+            if (nsch_) LB_BCUDA(cudaMemcpy(sch_, sch.data(), sizeof(int2) * nsch_, cudaMemcpyHostToDevice));
+        }
         LB_BCUDA(cudaMalloc((void**)&bch_, sizeof(int2) * std::max(1, nbch_)));
         LB_BCUDA(cudaMalloc((void**)&fch_, sizeof(int2) * std::max(1, nfch_)));
         if (nbch_) LB_BCUDA(cudaMemcpy(bch_, bch.data(), sizeof(int2) * nbch_, cudaMemcpyHostToDevice));
@@ -248,8 +287,10 @@ class BatchEngine final : public IBatch {
         policy_ = policy;
         std::vector<std::vector<int4>> per(doms_.size());
         for (size_t i = 0; i < doms_.size() && policy == 3; ++i)
-            for (int c = 0; c * FLUID_BLOCK < doms_[i]->host_nfl(); ++c) per[i].push_back(make_int4((int)i, c, 0, 0));
+            if (!doms_[i]->sparse())
+                for (int c = 0; c * FLUID_BLOCK < doms_[i]->host_nfl(); ++c) per[i].push_back(make_int4((int)i, c, 0, 0));
         for (size_t i = 0; i < doms_.size() && policy != 3; ++i) {
+            if (doms_[i]->sparse()) continue;  // its fluid chunks are fixed (sch_)
             const Geo& g = doms_[i]->geo();
             int tw = 128;
             if (policy == 0)
@@ -299,21 +340,26 @@ class BatchEngine final : public IBatch {
     // depends only on the boundary phase.
     int enqueue(cudaStream_t st, bool odd, std::string& err) {
         const int gf = std::min(grid_, std::max(1, ntiles_));
+        const int gs = std::min(grid_, std::max(1, nsch_));
         const int gb = std::min(grid_, std::max(1, nbch_));
         const int ge = std::min(grid_, std::max(1, nfch_));
         LB_BCUDA(cudaEventRecord(fork_, st));
         LB_BCUDA(cudaStreamWaitEvent(aux_, fork_, 0));
         if (nbch_) {
-            if (odd) kb_bound<T, LG, true><<<gb, LIST_BLOCK, 0, aux_>>>(dd_, bch_, nbch_);
-            else kb_bound<T, LG, false><<<gb, LIST_BLOCK, 0, aux_>>>(dd_, bch_, nbch_);
+            if (odd) kb_bound<T, LF, LG, true><<<gb, LIST_BLOCK, 0, aux_>>>(dd_, bch_, nbch_);
+            else kb_bound<T, LF, LG, false><<<gb, LIST_BLOCK, 0, aux_>>>(dd_, bch_, nbch_);
         }
         if (nfch_) kb_fend<T, LG><<<ge, LIST_BLOCK, 0, aux_>>>(dd_, fch_, nfch_);
         LB_BCUDA(cudaEventRecord(join_, aux_));
-        if (policy_ == 3) {
+        if (nsch_) {
+            if (odd) kb_fluid_sp<T, LF, LG, true><<<gs, FLUID_BLOCK, 0, st>>>(dd_, sch_, nsch_);
+            else kb_fluid_sp<T, LF, LG, false><<<gs, FLUID_BLOCK, 0, st>>>(dd_, sch_, nsch_);
+        }
+        if (ntiles_ && policy_ == 3) {
             // list chunks are stored in the tile array as {domain, chunk, 0, 0}
             if (odd) kb_fluid_list4<T, LF, LG, true><<<gf, FLUID_BLOCK, 0, st>>>(dd_, tiles_, ntiles_);
             else kb_fluid_list4<T, LF, LG, false><<<gf, FLUID_BLOCK, 0, st>>>(dd_, tiles_, ntiles_);
-        } else {
+        } else if (ntiles_) {
             if (odd) kb_fluid<T, LF, LG, true><<<gf, FLUID_BLOCK, 0, st>>>(dd_, tiles_, ntiles_);
             else kb_fluid<T, LF, LG, false><<<gf, FLUID_BLOCK, 0, st>>>(dd_, tiles_, ntiles_);
         }
@@ -368,6 +414,8 @@ class BatchEngine final : public IBatch {
         if (tiles_) cudaFree(tiles_);
         if (bch_) cudaFree(bch_);
         if (fch_) cudaFree(fch_);
+        if (sch_) cudaFree(sch_);
+        sch_ = nullptr;
         dd_ = nullptr;
         tiles_ = nullptr;
         bch_ = fch_ = nullptr;
@@ -384,8 +432,8 @@ class BatchEngine final : public IBatch {
     std::vector<std::unique_ptr<Engine<T, LF, LG>>> doms_;
     DomainDesc<T>* dd_ = nullptr;
     int4* tiles_ = nullptr;
-    int2 *bch_ = nullptr, *fch_ = nullptr;
-    int ntiles_ = 0, nbch_ = 0, nfch_ = 0, grid_ = 0, policy_ = 0;
+    int2 *bch_ = nullptr, *fch_ = nullptr, *sch_ = nullptr;
+    int ntiles_ = 0, nbch_ = 0, nfch_ = 0, nsch_ = 0, grid_ = 0, policy_ = 0;
     int lastodd_ = 1;
     cudaStream_t own_ = nullptr, aux_ = nullptr;
     cudaEvent_t fork_ = nullptr, join_ = nullptr;

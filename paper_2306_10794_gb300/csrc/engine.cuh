@@ -510,23 +510,27 @@ struct SparseSrc {
     T* Fw;
     T* Gw;
     __device__ __forceinline__ uint32_t e(int k) const { return __ldg(et + 32 * k); }
+    // slot E[k] + 32 d: the sum is formed in 32-bit unsigned arithmetic (an
+    // inactive neighbour's entry wraps around and the sum comes back to the
+    // own slot) before it offsets a pointer
+    __device__ __forceinline__ uint32_t slot(int k, int d) const { return e(k) + 32u * (uint32_t)d; }
     __device__ __forceinline__ T f(int i, bool) const {
         if (!ODD || i == 0) return ld_pop(F + pslot<LF>(i, n));
         const int d = LF::opp(i);
-        return ld_pop(F + e(d - 1) + 32u * (uint32_t)d);
+        return ld_pop(F + slot(d - 1, d));
     }
     __device__ __forceinline__ T g(int i, bool) const {
         if (!ODD || i == 0) return ld_pop(G + pslot<LG>(i, n));
         const int d = LG::opp(i);
-        return ld_pop(G + e(QF1 + d - 1) + 32u * (uint32_t)d);
+        return ld_pop(G + slot(QF1 + d - 1, d));
     }
     __device__ __forceinline__ void fput(int i, T v, bool) const {
         if (!ODD || i == 0) st_pop(Fw + pslot<LF>(LF::opp(i), n), v);
-        else st_pop(Fw + e(i - 1) + 32u * (uint32_t)i, v);
+        else st_pop(Fw + slot(i - 1, i), v);
     }
     __device__ __forceinline__ void gput(int i, T v, bool) const {
         if (!ODD || i == 0) st_pop(Gw + pslot<LG>(LG::opp(i), n), v);
-        else st_pop(Gw + e(QF1 + i - 1) + 32u * (uint32_t)i, v);
+        else st_pop(Gw + slot(QF1 + i - 1, i), v);
     }
 };
 
@@ -661,23 +665,29 @@ __global__ void __launch_bounds__(FLUID_BLOCK, sizeof(T) == 4 ? 8 : 5) k_fluid(c
 // compact order (cells fluid at the last packing first, row-major), so a
 // warp's 32 cells read and write whole 128-byte population lines whatever
 // the geometry.
+// One stored cell n of the active-cell layout (nothing unless it is fluid);
+// shared by the single-domain and batched sweeps.
+template <typename T, class LF, class LG, bool ODD>
+__device__ __forceinline__ void sparse_cell(const Dev<T>& a, const Phys& p, const PhysT<T>& q, int n) {
+    const uint32_t w = a.nwc[n];
+    if ((w & 3u) != CLS_FLUID) return;
+    const bool inlet = (w & NW_INLET) != 0u, outlet = (w & NW_OUTLET) != 0u;
+    uint32_t id = 0;
+    int x = 0, y = 0, z = 0;
+    if (inlet || outlet || a.tape_u) {
+        id = (uint32_t)a.cid[n];
+        coords(a.geo, id, x, y, z);
+    }
+    constexpr int NT = SparseSrc<T, LF, LG, ODD>::NT;
+    const SparseSrc<T, LF, LG, ODD> src{a.F, a.G, a.etab + etab_at((uint32_t)n, NT, 0), (uint32_t)n, a.F, a.G};
+    fluid_cell_src<T, LF, LG, ODD>(a, p, q, id, w, src, inlet, outlet, y, z);
+}
+
 template <typename T, class LF, class LG, bool ODD>
 __global__ void __launch_bounds__(FLUID_BLOCK, sizeof(T) == 4 ? 8 : 5) k_fluid_sp(const Dev<T> a, const Phys p, const PhysT<T> q) {
     const int ns = *a.ns;
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < ns; n += gridDim.x * blockDim.x) {
-        const uint32_t w = a.nwc[n];
-        if ((w & 3u) != CLS_FLUID) continue;
-        const bool inlet = (w & NW_INLET) != 0u, outlet = (w & NW_OUTLET) != 0u;
-        uint32_t id = 0;
-        int x = 0, y = 0, z = 0;
-        if (inlet || outlet || a.tape_u) {
-            id = (uint32_t)a.cid[n];
-            coords(a.geo, id, x, y, z);
-        }
-        constexpr int NT = SparseSrc<T, LF, LG, ODD>::NT;
-        const SparseSrc<T, LF, LG, ODD> src{a.F, a.G, a.etab + etab_at((uint32_t)n, NT, 0), (uint32_t)n, a.F, a.G};
-        fluid_cell_src<T, LF, LG, ODD>(a, p, q, id, w, src, inlet, outlet, y, z);
-    }
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < ns; n += gridDim.x * blockDim.x)
+        sparse_cell<T, LF, LG, ODD>(a, p, q, n);
 }
 
 // The same sweep over the compacted fluid cells: every lane of a warp has a

@@ -511,6 +511,8 @@ class Engine final : public ISim {
     void set_batched() { batched_ = true; }
     void force_list(bool v) { force_list_ = v; }
     void force_dense(bool v) { force_dense_ = v; }
+    bool sparse() const { return d_.sparse != 0; }
+    long long stored0() const { return ns0_; }
     bool uses_list() const { return d_.use_fl != 0; }
     double lane_efficiency() const { return lane_eff_; }
     int host_nfl() const { return (int)nfluid_; }

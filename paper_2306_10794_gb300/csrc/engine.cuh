@@ -573,11 +573,13 @@ __device__ __forceinline__ void fluid_cell_src(const Dev<T>& a, const Phys& p, c
         const int face = y + g.ny * z;
         if constexpr (QF > 0) {
             if (inlet) {
-                // moving-wall bounce-back with the inlet velocity (rho_w = 1)
+                // moving-wall bounce-back with the inlet velocity (rho_w = 1):
+                // f_i += 2 (w_i / cs^2) c_x u_in, with the exact-sum coefficients
+                // so that the injected mass is exactly u_in per cell and step
                 const T uin = T(a.inlet_ux[face]);
 #pragma unroll
                 for (int i = 1; i < QF; ++i)
-                    if (LF::cx(i) > 0) f[i] += T(6.0 * LF::w(i) * LF::cx(i)) * uin;
+                    if (LF::cx(i) > 0) f[i] += T(2 * LF::cx(i)) * mom_coef<LF, T>(i) * uin;
             }
             if (outlet) {
                 // pressure anti-bounce-back at rho_out with the previous velocity,

@@ -505,20 +505,25 @@ def adjoint_arm(a):
     K = max(4, a.steps)
     stream = torch.cuda.current_stream()
     fwd = lbrbc.Sim(p, mask, k_field=kf)
+    lay = fwd.layout_info()["layout"]
     fwd.step(3, stream=stream.cuda_stream)
     torch.cuda.synchronize()
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
     t0 = time.perf_counter()
     fwd.step(K, stream=stream.cuda_stream)
     torch.cuda.synchronize()
     t_f = time.perf_counter() - t0
+    ck_f = clocks.stop()
     fwd.close()
     adj = lbrbc.Sim(p, mask, k_field=kf)
     adj.step(3, stream=stream.cuda_stream)
     torch.cuda.synchronize()
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
     t0 = time.perf_counter()
     J, dk, dc, g = adj.adjoint(K, field=True)
     torch.cuda.synchronize()
     t_a = time.perf_counter() - t0
+    ck = clocks.stop()
     fluid = adj.info()["fluid_cells"]
     adj.close()
     line = {"metric": METRIC, "value": t_a / t_f, "unit": "adjoint/forward time", "n_gpus": 1, "steps": K,
@@ -530,7 +535,7 @@ def adjoint_arm(a):
                        "fluid_cells": fluid},
             "forward_ms_per_step": t_f / K * 1e3, "adjoint_ms_per_step": t_a / K * 1e3,
             "J": J, "dJ_dk": dk, "dJ_dceq": dc, "dJ_dkfield_norm": float(np.sqrt((g ** 2).sum())),
-            "gpu_launches": None}
+            "layout": lay, "clocks": ck, "clocks_forward": ck_f, "gpu_launches": None}
     print(json.dumps(line), flush=True)
     return 0
 

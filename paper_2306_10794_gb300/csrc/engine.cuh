@@ -62,6 +62,16 @@ constexpr uint32_t BW_DIRICHLET = 1u << 16;
 #ifndef LBRBC_STREAM_HINT
 #define LBRBC_STREAM_HINT 1
 #endif
+// Active-cell sweep: cache policy of the odd step's loads through the
+// neighbour table (1 evict-first like the other population accesses, 0 the
+// default policy, which keeps partly read lines for the neighbouring warps)
+// and resident blocks of 128 threads per SM it is compiled for.
+#ifndef LBRBC_SP_NBR_HINT
+#define LBRBC_SP_NBR_HINT 1
+#endif
+#ifndef LBRBC_SP_BLOCKS
+#define LBRBC_SP_BLOCKS 8
+#endif
 constexpr int FLUID_BLOCK = LBRBC_FLUID_BLOCK;
 constexpr int LIST_BLOCK = 256;
 constexpr int SCAN_CHUNK = 1024;
@@ -514,15 +524,22 @@ struct SparseSrc {
     // inactive neighbour's entry wraps around and the sum comes back to the
     // own slot) before it offsets a pointer
     __device__ __forceinline__ uint32_t slot(int k, int d) const { return e(k) + 32u * (uint32_t)d; }
+    __device__ __forceinline__ T ld_nbr(const T* p) const {
+#if LBRBC_SP_NBR_HINT
+        return ld_pop(p);
+#else
+        return *p;
+#endif
+    }
     __device__ __forceinline__ T f(int i, bool) const {
         if (!ODD || i == 0) return ld_pop(F + pslot<LF>(i, n));
         const int d = LF::opp(i);
-        return ld_pop(F + slot(d - 1, d));
+        return ld_nbr(F + slot(d - 1, d));
     }
     __device__ __forceinline__ T g(int i, bool) const {
         if (!ODD || i == 0) return ld_pop(G + pslot<LG>(i, n));
         const int d = LG::opp(i);
-        return ld_pop(G + slot(QF1 + d - 1, d));
+        return ld_nbr(G + slot(QF1 + d - 1, d));
     }
     __device__ __forceinline__ void fput(int i, T v, bool) const {
         if (!ODD || i == 0) st_pop(Fw + pslot<LF>(LF::opp(i), n), v);
@@ -686,7 +703,7 @@ __device__ __forceinline__ void sparse_cell(const Dev<T>& a, const Phys& p, cons
 }
 
 template <typename T, class LF, class LG, bool ODD>
-__global__ void __launch_bounds__(FLUID_BLOCK, sizeof(T) == 4 ? 8 : 5) k_fluid_sp(const Dev<T> a, const Phys p, const PhysT<T> q) {
+__global__ void __launch_bounds__(FLUID_BLOCK, sizeof(T) == 4 ? LBRBC_SP_BLOCKS : 5) k_fluid_sp(const Dev<T> a, const Phys p, const PhysT<T> q) {
     const int ns = *a.ns;
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < ns; n += gridDim.x * blockDim.x)
         sparse_cell<T, LF, LG, ODD>(a, p, q, n);

@@ -53,6 +53,7 @@ constexpr int GBIT = 20;
 // bits 8.. link towards a fluid cell (o = 1..QG-1), bit 16 Dirichlet cell.
 constexpr int BW_LINK = 8;
 constexpr uint32_t BW_DIRICHLET = 1u << 16;
+constexpr uint32_t BW_DEAD = 1u << 17;  // entry of a cell that is no longer a wet boundary cell
 
 #ifndef LBRBC_FLUID_BLOCK
 #define LBRBC_FLUID_BLOCK 128
@@ -234,7 +235,17 @@ struct Dev {
     uint32_t* etab;       // effective block bases of each stored cell's neighbours (see k_sp_tables),
                           // blocked by 32 cells: (QF - 1) flow then (QG - 1) solute entries per cell
     int* b_cn;            // cap_b: compact index of each wet boundary cell
-    int* rown;            // NP: owner of a cell of the event region (-1 outside), sparse event path
+    int* rown;            // NP: owner of a cell of the event region (RNONE outside), event path
+    // local maintenance of the classes and lists after phase-change events
+    // (null without phase change, or with LBRBC_LOCAL_LISTS=0): fluid-end
+    // position of every cell (-1: none), the step's candidates, counters,
+    // and the cells of the step's region
+    int* fmap;            // NP
+    int* candb;           // LOC_CAND_CAP: new wet boundary cells of the step
+    int* candf;           // LOC_CAND_CAP: new fluid ends of the step
+    int* lcnt;            // LC_N counters (LC_*)
+    uint32_t* lmark;      // NP: step stamp of the cells of the region
+    int* rlist;           // LOC_EV_MAX * cube: cells of the region
     int* repack;          // [0] set when a cell needs storage it does not have
     int* nrepack;         // repackings done
     // repacking targets (phase change only): new numbering and populations
@@ -918,9 +929,10 @@ __device__ __forceinline__ void bound_entry(const Dev<T>& a, const Phys& p, cons
     T* __restrict__ G = a.G;
     const T cref = q.cref;
     const T gam = q.gamma, ics2 = q.ics2;
+    const uint32_t bw = a.b_word[e];
+    if (bw & BW_DEAD) return;
     const BoundSlots<T, LF, LG, ODD, SP> kb(a, e);
     const uint32_t b = (uint32_t)a.b_idx[e];
-    const uint32_t bw = a.b_word[e];
     T gp[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -1044,6 +1056,7 @@ __global__ void __launch_bounds__(LIST_BLOCK, 4) k_bound(const Dev<T> a, const P
 template <typename T, class LG>
 __device__ __forceinline__ void fend_entry(const Dev<T>& a, const Phys& p, int e) {
     const long long f = a.f_idx[e];
+    if (f < 0) return;  // no longer a fluid end
     T acc = T(0);
 #pragma unroll
     for (int o = 1; o < LG::Q; ++o) acc += a.f_share[(long long)(o - 1) * a.cap_f + e];
@@ -1337,64 +1350,336 @@ __global__ void k_ev_neighbours(const Dev<T> a, const Phys p, int lastodd) {
     }
 }
 
-// New classes and node words from the kinds (whole grid); boundary cells
-// that lost their last fluid neighbour convert their solute into phi, solid
-// cells that gained one start empty.
+// New class and node word of in-grid cell (x, y, z) from the kinds; a
+// boundary cell that lost its last fluid neighbour converts its solute into
+// phi, a solid cell that gained one starts empty.  force: creation (no state
+// to convert).
+template <typename T, class LF, class LG>
+__device__ void reclassify_cell(const Dev<T>& a, const Phys& p, int x, int y, int z, long long id, int lastodd,
+                                int force) {
+    const Geo& g = a.geo;
+    const uint32_t cls = class_of<LG>(g, a.kind, x, y, z);
+    const uint32_t old = a.nw[id] & 3u;
+    if (!force && old != cls && a.evidx[id] < 0) {
+        const Nbr d = nbr_deltas(g, x, y, z);
+        if (old == CLS_BOUND && cls == CLS_SOLID) {
+            const double C = p.cref + (double)post_sum<LG, false, T>(a, a.G, id, d, lastodd);
+            if (a.kind[id] == KIND_REACTIVE) a.phi[id] += p.Vm * C;
+            else fx_add(a.facc, -C);
+        }
+        if (cls != CLS_FLUID) {
+            if (a.sparse && a.cmap[id] < 0) {
+                // a solid cell outside the stored set gained a fluid
+                // neighbour: the layout is repacked before the next step,
+                // and the repacking gives it its starting populations
+                *a.repack = 1;
+            } else {
+#pragma unroll
+                for (int i = 0; i < LG::Q; ++i)
+                    a.G[post_slot<LG, false, T>(a, id, d, i, lastodd)] = T(-gweight<LG>(p, i) * p.cref);
+            }
+        }
+    }
+    uint32_t w = cls;
+    if (cls == CLS_FLUID) {
+        if constexpr (LF::Q > 0) {
+#pragma unroll
+            for (int i = 1; i < LF::Q; ++i) {
+                int xx = x - LF::cx(i), yy = y - LF::cy(i), zz = z - LF::cz(i);
+                if (class_at<LG>(g, a.kind, xx, yy, zz) != CLS_FLUID) w |= 1u << (FBIT + i - 1);
+            }
+        }
+#pragma unroll
+        for (int i = 1; i < LG::Q; ++i) {
+            int xx = x - LG::cx(i), yy = y - LG::cy(i), zz = z - LG::cz(i);
+            if (class_at<LG>(g, a.kind, xx, yy, zz) == CLS_SOLID) w |= 1u << (GBIT + i - 1);
+        }
+        if (g.open_x && x == 0) w |= NW_INLET;
+        if (g.open_x && x == g.nx - 1) w |= NW_OUTLET;
+    }
+    a.nw[id] = w;
+    if (a.sparse) {
+        const int c = a.cmap[id];
+        if (c >= 0) a.nwc[c] = w;
+    }
+}
+
+// Local list maintenance: counters in Dev::lcnt.
+enum {
+    LC_CANDB = 0,   // new wet boundary cells of this step
+    LC_CANDF = 1,   // new fluid ends of this step
+    LC_DEADB = 2,   // dead boundary entries since the last compaction
+    LC_DEADF = 3,   // dead fluid-end entries since the last compaction
+    LC_FULL = 4,    // this step reclassifies the whole grid / compacts the lists
+    LC_LOCAL = 5,   // this step updates the region around the events only
+    LC_BASEB = 6,   // list lengths before this step's appends
+    LC_BASEF = 7,
+    LC_NREG = 8,    // cells of this step's region
+    LC_N = 16
+};
+// Cells that a change of kind at an event cell can affect: a cell's class
+// depends on the kinds of its solute-lattice neighbours, a node word on the
+// classes of its flow- and solute-lattice neighbours, a boundary entry on the
+// kinds within two solute links and the wall normal's D3Q19 / D2Q9 stencil,
+// and a cell's fluid-end status on the classes of its solute-lattice
+// neighbours.  Every such offset lies in the cube of half width 2.
+constexpr int LOC_HALF = 2;
+constexpr int LOC_CAND_CAP = 8192;    // appends per list and step (more: full compaction)
+constexpr int LOC_EV_MAX = 16384;     // events of a step handled locally (more: whole grid)
+
+template <int DIM>
+__host__ __device__ constexpr int loc_cube() {
+    return DIM == 3 ? (2 * LOC_HALF + 1) * (2 * LOC_HALF + 1) * (2 * LOC_HALF + 1)
+                    : (2 * LOC_HALF + 1) * (2 * LOC_HALF + 1);
+}
+
+// List entry of wet boundary cell (x, y, z) at position pos: its index,
+// coordinates and compact index, its word (inactive sources, links to fluid
+// cells, Dirichlet flag), the link coefficients (e_o . n)+ of the wall normal
+// and its rate.  The share slots are set by the caller.
+template <typename T, class LG>
+__device__ void bound_entry_data(const Dev<T>& a, const Phys& p, int x, int y, int z, long long id, int pos) {
+    const Geo& g = a.geo;
+    a.b_idx[pos] = (int)id;
+    if (a.sparse) a.b_cn[pos] = a.cmap[id];
+    a.b_xyz[pos] = pack_xyz(x, y, z);
+    uint32_t bw = 0;
+    const uint8_t kd = a.kind[id];
+    if (kd == KIND_DIRICHLET) bw |= BW_DIRICHLET;
+    double nrm[3];
+    const bool ok = wall_normal<LG::DIM>(g, a.kind, x, y, z, nrm);
+#pragma unroll
+    for (int o = 1; o < LG::Q; ++o) {
+        int xs = x - LG::cx(o), ys = y - LG::cy(o), zs = z - LG::cz(o);
+        if (class_at<LG>(g, a.kind, xs, ys, zs) == CLS_SOLID) bw |= 1u << (o - 1);
+        int xf = x + LG::cx(o), yf = y + LG::cy(o), zf = z + LG::cz(o);
+        T kap = T(0);
+        if (wrap_inside(g, xf, yf, zf) && a.kind[g.idx(xf, yf, zf)] == KIND_FLUID) {
+            bw |= 1u << (BW_LINK + o - 1);
+            double kk = 1.0;
+            if (ok) {
+                kk = LG::cx(o) * nrm[0] + LG::cy(o) * nrm[1] + LG::cz(o) * nrm[2];
+                kk = kk > 0.0 ? kk : 0.0;
+            }
+            kap = T(kk);
+        }
+        a.b_kappa[(long long)(o - 1) * a.cap_b + pos] = kap;
+    }
+    a.b_word[pos] = bw;
+    if (a.b_krate) a.b_krate[pos] = a.kfield ? a.kfield[id] : p.k_r;
+}
+
+// Whether the full compaction of the lists runs: at creation, when the
+// local maintenance asked for it, or (without local maintenance) on every
+// step with events.
+template <typename T>
+__device__ __forceinline__ bool full_lists(const Dev<T>& a, int force) {
+    return force || (a.lcnt ? a.lcnt[LC_FULL] != 0 : *a.nev != 0);
+}
+
+// New classes and node words from the kinds over the whole grid: at
+// creation, and in a step whose events are too many for the local update.
 template <typename T, class LF, class LG>
 __global__ void k_reclassify(const Dev<T> a, const Phys p, int lastodd, int force) {
-    if (!force && *a.nev == 0) return;
+    if (!force && !(a.lcnt ? a.lcnt[LC_FULL] != 0 : *a.nev != 0)) return;
     const Geo& g = a.geo;
-    const long long NP = g.NP;
     const long long total = (long long)g.nx * g.ny * g.nz;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(t % g.nx);
         const int y = (int)((t / g.nx) % g.ny);
         const int z = (int)(t / ((long long)g.nx * g.ny));
+        reclassify_cell<T, LF, LG>(a, p, x, y, z, g.idx(x, y, z), lastodd, force);
+    }
+}
+
+// Whether this step's events are handled locally (one thread).
+template <typename T>
+__global__ void k_loc_decide(const Dev<T> a) {
+    int* c = a.lcnt;
+    c[LC_CANDB] = c[LC_CANDF] = c[LC_NREG] = 0;
+    const int nev = *a.nev;
+    const bool any = nev > 0;
+    const bool local = any && nev <= LOC_EV_MAX && nev <= a.cap_e;
+    c[LC_LOCAL] = local;
+    c[LC_FULL] = any && !local;
+}
+
+// Cell of the region: offset t of the cube around event e, wrapped into the
+// grid; false outside it.
+template <class LG>
+__device__ __forceinline__ bool loc_cell(const Geo& g, const int* ev_node, long long t, int& x, int& y, int& z) {
+    constexpr int W = 2 * LOC_HALF + 1, NC = loc_cube<LG::DIM>();
+    const int e = (int)(t / NC), j = (int)(t % NC);
+    coords(g, ev_node[e], x, y, z);
+    x += j % W - LOC_HALF;
+    y += (j / W) % W - LOC_HALF;
+    if (LG::DIM == 3) z += j / (W * W) - LOC_HALF;
+    return wrap_inside(g, x, y, z);
+}
+
+// Local reclassification: every cell of the cubes around the events once
+// (a per-step stamp claims it), recorded in the region list.
+template <typename T, class LF, class LG>
+__global__ void k_loc_recl(const Dev<T> a, const Phys p, int lastodd) {
+    if (!a.lcnt[LC_LOCAL]) return;
+    const Geo& g = a.geo;
+    const long long total = (long long)*a.nev * loc_cube<LG::DIM>();
+    const uint32_t stamp = (uint32_t)*a.step + 1u;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        if (!loc_cell<LG>(g, a.ev_node, t, x, y, z)) continue;
         const long long id = g.idx(x, y, z);
-        const uint32_t cls = class_of<LG>(g, a.kind, x, y, z);
-        const uint32_t old = a.nw[id] & 3u;
-        if (!force && old != cls && a.evidx[id] < 0) {
-            const Nbr d = nbr_deltas(g, x, y, z);
-            if (old == CLS_BOUND && cls == CLS_SOLID) {
-                const double C = p.cref + (double)post_sum<LG, false, T>(a, a.G, id, d, lastodd);
-                if (a.kind[id] == KIND_REACTIVE) a.phi[id] += p.Vm * C;
-                else fx_add(a.facc, -C);
-            }
-            if (cls != CLS_FLUID) {
-                if (a.sparse && a.cmap[id] < 0) {
-                    // a solid cell outside the stored set gained a fluid
-                    // neighbour: the layout is repacked before the next step,
-                    // and the repacking gives it its starting populations
-                    *a.repack = 1;
-                } else {
+        if (atomicExch(&a.lmark[id], stamp) == stamp) continue;
+        reclassify_cell<T, LF, LG>(a, p, x, y, z, id, lastodd, 0);
+        a.rlist[atomicAdd(&a.lcnt[LC_NREG], 1)] = (int)id;
+    }
+}
+
+// Whether fluid cell (x, y, z) is a fluid end: a reactive wet boundary cell
+// upstream along a solute link.
+template <typename T, class LG>
+__device__ __forceinline__ bool is_fluid_end(const Dev<T>& a, int x, int y, int z) {
+    const Geo& g = a.geo;
 #pragma unroll
-                    for (int i = 0; i < LG::Q; ++i)
-                        a.G[post_slot<LG, false, T>(a, id, d, i, lastodd)] = T(-gweight<LG>(p, i) * p.cref);
+    for (int o = 1; o < LG::Q; ++o) {
+        int xx = x - LG::cx(o), yy = y - LG::cy(o), zz = z - LG::cz(o);
+        if (!wrap_inside(g, xx, yy, zz)) continue;
+        const long long nb = g.idx(xx, yy, zz);
+        if ((a.nw[nb] & 3u) == CLS_BOUND && a.kind[nb] == KIND_REACTIVE) return true;
+    }
+    return false;
+}
+
+// Region cells against the lists: boundary entries of cells that stay wet
+// boundary cells are recomputed in place, entries of cells that left a list
+// are marked dead, cells that joined one become candidates.
+template <typename T, class LG>
+__global__ void k_loc_lists(const Dev<T> a, const Phys p) {
+    if (!a.lcnt[LC_LOCAL] || a.lcnt[LC_FULL]) return;
+    const Geo& g = a.geo;
+    const int n = a.lcnt[LC_NREG];
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const long long id = a.rlist[r];
+        int x, y, z;
+        coords(g, id, x, y, z);
+        const uint32_t cls = a.nw[id] & 3u;
+        const int pb = a.bmap[id];
+        if (cls == CLS_BOUND) {
+            if (pb >= 0) {
+                bound_entry_data<T, LG>(a, p, x, y, z, id, pb);
+            } else {
+                const int k = atomicAdd(&a.lcnt[LC_CANDB], 1);
+                if (k < LOC_CAND_CAP) a.candb[k] = (int)id;
+            }
+        } else if (pb >= 0) {
+            a.b_word[pb] = BW_DEAD;
+            a.bmap[id] = -1;
+            atomicAdd(&a.lcnt[LC_DEADB], 1);
+        }
+        const bool fe = cls == CLS_FLUID && is_fluid_end<T, LG>(a, x, y, z);
+        const int pf = a.fmap[id];
+        if (fe && pf < 0) {
+            const int k = atomicAdd(&a.lcnt[LC_CANDF], 1);
+            if (k < LOC_CAND_CAP) a.candf[k] = (int)id;
+        } else if (!fe && pf >= 0) {
+            a.f_idx[pf] = -1;
+            a.fmap[id] = -1;
+            atomicAdd(&a.lcnt[LC_DEADF], 1);
+        }
+    }
+}
+
+// Room for the appends, or a full compaction instead (too many candidates,
+// no capacity left, or more than an eighth of a list dead); one thread.
+template <typename T>
+__global__ void k_loc_plan(const Dev<T> a) {
+    int* c = a.lcnt;
+    if (!c[LC_LOCAL] || c[LC_FULL]) return;
+    const int cb = c[LC_CANDB], cf = c[LC_CANDF];
+    const long long nb = *a.nb, nf = *a.nf;
+    if (cb > LOC_CAND_CAP || cf > LOC_CAND_CAP || nb + cb > a.cap_b || nf + cf > a.cap_f ||
+        8LL * c[LC_DEADB] > nb + cb || 8LL * c[LC_DEADF] > nf + cf) {
+        c[LC_FULL] = 1;
+        return;
+    }
+    c[LC_BASEB] = (int)nb;
+    c[LC_BASEF] = (int)nf;
+    *a.nb = (int)(nb + cb);
+    *a.nf = (int)(nf + cf);
+}
+
+// Appends in cell order (rank among the candidates), so that the lists do
+// not depend on thread timing.
+template <typename T, class LG>
+__global__ void k_loc_append(const Dev<T> a, const Phys p) {
+    if (!a.lcnt[LC_LOCAL] || a.lcnt[LC_FULL]) return;
+    const Geo& g = a.geo;
+    const int cb = a.lcnt[LC_CANDB], cf = a.lcnt[LC_CANDF];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cb + cf; t += gridDim.x * blockDim.x) {
+        const bool isb = t < cb;
+        const int* cand = isb ? a.candb : a.candf;
+        const int nc = isb ? cb : cf;
+        const int id = cand[isb ? t : t - cb];
+        int rank = 0;
+        for (int k = 0; k < nc; ++k) rank += cand[k] < id;
+        if (isb) {
+            const int pos = a.lcnt[LC_BASEB] + rank;
+            int x, y, z;
+            coords(g, id, x, y, z);
+            a.bmap[id] = pos;
+            bound_entry_data<T, LG>(a, p, x, y, z, id, pos);
+        } else {
+            const int pos = a.lcnt[LC_BASEF] + rank;
+            a.f_idx[pos] = id;
+            a.fmap[id] = pos;
+#pragma unroll
+            for (int o = 1; o < LG::Q; ++o) a.f_share[(long long)(o - 1) * a.cap_f + pos] = T(0);
+        }
+    }
+}
+
+// Share slots of the boundary entries of the region: link o of a reactive
+// wet boundary cell feeds the fluid end downstream of it.  A fluid end of the
+// region clears the shares of links whose source is gone (nothing writes
+// them any more).  Entries outside the region keep their slots: neither end
+// of their links changed.
+template <typename T, class LG>
+__global__ void k_loc_fslot(const Dev<T> a) {
+    if (!a.lcnt[LC_LOCAL] || a.lcnt[LC_FULL]) return;
+    const Geo& g = a.geo;
+    const int n = a.lcnt[LC_NREG];
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const long long id = a.rlist[r];
+        int x, y, z;
+        coords(g, id, x, y, z);
+        const int pf = a.fmap[id];
+        if (pf >= 0) {
+#pragma unroll
+            for (int o = 1; o < LG::Q; ++o) {
+                int xs = x - LG::cx(o), ys = y - LG::cy(o), zs = z - LG::cz(o);
+                bool src = false;
+                if (wrap_inside(g, xs, ys, zs)) {
+                    const long long nb = g.idx(xs, ys, zs);
+                    src = (a.nw[nb] & 3u) == CLS_BOUND && a.kind[nb] == KIND_REACTIVE;
                 }
+                if (!src) a.f_share[(long long)(o - 1) * a.cap_f + pf] = T(0);
             }
         }
-        uint32_t w = cls;
-        if (cls == CLS_FLUID) {
-            if constexpr (LF::Q > 0) {
+        const int pb = a.bmap[id];
+        if (pb < 0) continue;
+        const bool reactive = a.kind[id] == KIND_REACTIVE;
 #pragma unroll
-                for (int i = 1; i < LF::Q; ++i) {
-                    int xx = x - LF::cx(i), yy = y - LF::cy(i), zz = z - LF::cz(i);
-                    if (class_at<LG>(g, a.kind, xx, yy, zz) != CLS_FLUID) w |= 1u << (FBIT + i - 1);
-                }
+        for (int o = 1; o < LG::Q; ++o) {
+            int xf = x + LG::cx(o), yf = y + LG::cy(o), zf = z + LG::cz(o);
+            int slot = -1;
+            if (reactive && wrap_inside(g, xf, yf, zf)) {
+                const long long f = g.idx(xf, yf, zf);
+                const int pf = (a.nw[f] & 3u) == CLS_FLUID ? a.fmap[f] : -1;
+                if (pf >= 0) slot = (o - 1) * a.cap_f + pf;
             }
-#pragma unroll
-            for (int i = 1; i < LG::Q; ++i) {
-                int xx = x - LG::cx(i), yy = y - LG::cy(i), zz = z - LG::cz(i);
-                if (class_at<LG>(g, a.kind, xx, yy, zz) == CLS_SOLID) w |= 1u << (GBIT + i - 1);
-            }
-            if (g.open_x && x == 0) w |= NW_INLET;
-            if (g.open_x && x == g.nx - 1) w |= NW_OUTLET;
-        }
-        a.nw[id] = w;
-        if (a.sparse) {
-            const int c = a.cmap[id];
-            if (c >= 0) a.nwc[c] = w;
+            a.b_fslot[(long long)(o - 1) * a.cap_b + pb] = slot;
         }
     }
 }
@@ -1403,7 +1688,7 @@ __global__ void k_reclassify(const Dev<T> a, const Phys p, int lastodd, int forc
 // Pass 1: counts per chunk of SCAN_CHUNK cells.
 template <typename T, class LG>
 __global__ void k_count(const Dev<T> a, int which, int force, int nchunks) {
-    if (!force && *a.nev == 0) return;
+    if (!full_lists(a, force)) return;
     const Geo& g = a.geo;
     const long long total = (long long)g.nx * g.ny * g.nz;
     __shared__ int cnt;
@@ -1443,7 +1728,7 @@ __global__ void k_count(const Dev<T> a, int which, int force, int nchunks) {
 // Pass 2: exclusive scan of the chunk counts (one block); total -> *count.
 template <typename T>
 __global__ void k_scan(const Dev<T> a, int nchunks, int which, int force) {
-    if (!force && *a.nev == 0) return;
+    if (!full_lists(a, force)) return;
     __shared__ int part[1024];
     const int per = (nchunks + blockDim.x - 1) / blockDim.x;
     const int lo = threadIdx.x * per, hi = min(nchunks, lo + per);
@@ -1474,7 +1759,7 @@ __global__ void k_scan(const Dev<T> a, int nchunks, int which, int force) {
 // Pass 3: write the entries in cell order.
 template <typename T, class LG>
 __global__ void k_write_lists(const Dev<T> a, const Phys p, int which, int force, int nchunks) {
-    if (!force && *a.nev == 0) return;
+    if (!full_lists(a, force)) return;
     const Geo& g = a.geo;
     const long long total = (long long)g.nx * g.ny * g.nz;
     __shared__ int warp_tot[32];
@@ -1500,7 +1785,10 @@ __global__ void k_write_lists(const Dev<T> a, const Phys p, int which, int force
                 a.bmap[id] = -1;
             } else if (which == 2) {
                 sel = cls == CLS_FLUID;
-            } else if (cls == CLS_FLUID) {
+            } else if (a.fmap) {
+                a.fmap[id] = -1;
+            }
+            if (which == 1 && cls == CLS_FLUID) {
 #pragma unroll
                 for (int o = 1; o < LG::Q; ++o) {
                     src[o] = -1;
@@ -1525,40 +1813,15 @@ __global__ void k_write_lists(const Dev<T> a, const Phys p, int which, int force
         const int pos = base_s + woff + __popc(bal & ((1u << lane) - 1u));
         if (sel) {
             if (which == 0 && pos < a.cap_b) {
-                a.b_idx[pos] = (int)id;
-                if (a.sparse) a.b_cn[pos] = a.cmap[id];
-                a.b_xyz[pos] = pack_xyz(x, y, z);
                 a.bmap[id] = pos;
-                uint32_t bw = 0;
-                const uint8_t kd = a.kind[id];
-                if (kd == KIND_DIRICHLET) bw |= BW_DIRICHLET;
-                double nrm[3];
-                const bool ok = wall_normal<LG::DIM>(g, a.kind, x, y, z, nrm);
-#pragma unroll
-                for (int o = 1; o < LG::Q; ++o) {
-                    int xs = x - LG::cx(o), ys = y - LG::cy(o), zs = z - LG::cz(o);
-                    if (class_at<LG>(g, a.kind, xs, ys, zs) == CLS_SOLID) bw |= 1u << (o - 1);
-                    int xf = x + LG::cx(o), yf = y + LG::cy(o), zf = z + LG::cz(o);
-                    T kap = T(0);
-                    if (wrap_inside(g, xf, yf, zf) && a.kind[g.idx(xf, yf, zf)] == KIND_FLUID) {
-                        bw |= 1u << (BW_LINK + o - 1);
-                        double kk = 1.0;
-                        if (ok) {
-                            kk = LG::cx(o) * nrm[0] + LG::cy(o) * nrm[1] + LG::cz(o) * nrm[2];
-                            kk = kk > 0.0 ? kk : 0.0;
-                        }
-                        kap = T(kk);
-                    }
-                    a.b_kappa[(long long)(o - 1) * a.cap_b + pos] = kap;
-                }
-                a.b_word[pos] = bw;
-                if (a.b_krate) a.b_krate[pos] = a.kfield ? a.kfield[id] : p.k_r;
+                bound_entry_data<T, LG>(a, p, x, y, z, id, pos);
 #pragma unroll
                 for (int o = 1; o < LG::Q; ++o) a.b_fslot[(long long)(o - 1) * a.cap_b + pos] = -1;
             } else if (which == 2 && pos < a.cap_fl) {
                 a.fl_xyz[pos] = (uint32_t)x | ((uint32_t)y << 11) | ((uint32_t)z << 22);
             } else if (which == 1 && pos < a.cap_f) {
                 a.f_idx[pos] = (int)id;
+                if (a.fmap) a.fmap[id] = pos;
 #pragma unroll
                 for (int o = 1; o < LG::Q; ++o) {
                     const long long slot = (long long)(o - 1) * a.cap_f + pos;
@@ -1930,6 +2193,16 @@ __global__ void k_sp_repack_done(const Dev<T> a) {
     *a.nrepack += 1;
 }
 
+// Compact indices of the boundary entries after a repacking (the local list
+// maintenance keeps the entries and their order).
+template <typename T>
+__global__ void k_sp_recn(const Dev<T> a) {
+    if (*a.repack == 0) return;
+    const int n = *a.nb;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
+        if (!(a.b_word[e] & BW_DEAD)) a.b_cn[e] = a.cmap[a.b_idx[e]];
+}
+
 // -1 everywhere (cmap2 before a repacking), when one is pending.
 template <typename T>
 __global__ void k_sp_clear2(const Dev<T> a) {
@@ -1949,6 +2222,10 @@ template <typename T>
 __global__ void k_step_end(const Dev<T> a) {
     *a.nev = 0;
     *a.step += 1;
+    if (a.lcnt) {
+        if (a.lcnt[LC_FULL]) a.lcnt[LC_DEADB] = a.lcnt[LC_DEADF] = 0;
+        a.lcnt[LC_FULL] = a.lcnt[LC_LOCAL] = 0;
+    }
 }
 
 // Initial state: equilibrium populations written as an odd step would write

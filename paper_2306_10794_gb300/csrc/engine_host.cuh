@@ -196,6 +196,25 @@ class Engine final : public ISim {
                 LB_CUDA(dalloc(&d_.cmap2, (size_t)NP));
             }
         }
+        // local maintenance of classes and lists after events (default on;
+        // LBRBC_LOCAL_LISTS=0 reclassifies the whole grid and compacts the
+        // lists in every step with events)
+        d_.fmap = d_.candb = d_.candf = d_.lcnt = d_.rlist = nullptr;
+        d_.lmark = nullptr;
+        {
+            const char* env = getenv("LBRBC_LOCAL_LISTS");
+            if (P.phase_change && !(env && !strcmp(env, "0"))) {
+                LB_CUDA(dalloc(&d_.fmap, (size_t)NP));
+                LB_CUDA(cudaMemset(d_.fmap, 0xff, NP * sizeof(int)));
+                LB_CUDA(dalloc(&d_.lmark, (size_t)NP));
+                LB_CUDA(cudaMemset(d_.lmark, 0, NP * sizeof(uint32_t)));
+                LB_CUDA(dalloc(&d_.candb, (size_t)LOC_CAND_CAP));
+                LB_CUDA(dalloc(&d_.candf, (size_t)LOC_CAND_CAP));
+                LB_CUDA(dalloc(&d_.lcnt, (size_t)LC_N));
+                LB_CUDA(cudaMemset(d_.lcnt, 0, LC_N * sizeof(int)));
+                LB_CUDA(dalloc(&d_.rlist, (size_t)LOC_EV_MAX * loc_cube<LG::DIM>()));
+            }
+        }
         LB_CUDA(dalloc(&d_.nw, (size_t)NP));
         LB_CUDA(dalloc(&d_.kind, (size_t)NP));
         LB_CUDA(dalloc(&d_.phi, (size_t)NP));
@@ -870,6 +889,7 @@ class Engine final : public ISim {
         k_sp_commit<T, LF, LG><<<grid_for(d_.geo.NP, 256), 256, 0, st>>>(d_);
         k_sp_commit_end<T><<<1, 1, 0, st>>>(d_);
         k_sp_tables<T, LF, LG><<<grid_for(d_.cap_s, 256), 256, 0, st>>>(d_, d_.repack);
+        k_sp_recn<T><<<list_grid(d_.cap_b), LIST_BLOCK, 0, st>>>(d_);
         k_sp_repack_done<T><<<1, 1, 0, st>>>(d_);
     }
 
@@ -933,12 +953,25 @@ class Engine final : public ISim {
             k_ev_compute<T, LF, LG><<<eg, 256, 0, st>>>(d_, ph_, form);
             k_ev_apply_self<T, LF, LG><<<eg, 256, 0, st>>>(d_, ph_, form);
             k_ev_neighbours<T, LG><<<eg, 256, 0, st>>>(d_, ph_, form);
+            // Classes and lists: locally around the events (the cube of half
+            // width 2 around each), or over the whole grid when the events
+            // are many, the stored set was repacked or the lists need a
+            // compaction.
+            const bool loc = d_.lcnt != nullptr;
+            if (loc) k_loc_decide<T><<<1, 1, 0, st>>>(d_);
             enqueue_reclassify(st, form, 0);
+            if (loc) k_loc_recl<T, LF, LG><<<eg, 256, 0, st>>>(d_, ph_, form);
             if (sp) enqueue_repack(st);
             if (sp) k_sp_retab<T, LF, LG><<<eg, 256, 0, st>>>(d_);
             if (sp && odd) {
                 k_sp_swap<T, LF, LG><<<eg, 256, 0, st>>>(d_);
                 k_sp_rreset<T, LG><<<eg, 256, 0, st>>>(d_);
+            }
+            if (loc) {
+                k_loc_lists<T, LG><<<eg, 256, 0, st>>>(d_, ph_);
+                k_loc_plan<T><<<1, 1, 0, st>>>(d_);
+                k_loc_append<T, LG><<<eg, 256, 0, st>>>(d_, ph_);
+                k_loc_fslot<T, LG><<<eg, 256, 0, st>>>(d_);
             }
             enqueue_lists(st, 0);
             k_ev_reset<T><<<eg, 256, 0, st>>>(d_);
@@ -965,7 +998,8 @@ class Engine final : public ISim {
         int n = 3;
         if (ph_.phase_change) {
             n += 4 + 1 + 3 * (d_.use_fl ? 3 : 2) + 2;  // events, reclassification, lists, reset + step end
-            if (d_.sparse) n += 1 + (1 + 9 + 1) + 5 + 1 + 2;  // repacking (conditional), table refresh, swaps of odd steps / 2
+            if (d_.sparse) n += 1 + (1 + 9 + 1) + 6 + 1 + 2;  // repacking (conditional), table refresh, swaps of odd steps / 2
+            if (d_.lcnt) n += 6;                              // local reclassification and list maintenance
         }
         return n;
     }

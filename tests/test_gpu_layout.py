@@ -4,6 +4,8 @@ their fields, ledgers and phase-change events must agree bit for bit; the
 active-cell layout must also match the FP64 oracle where dissolution grows
 the pore space beyond the stored margin and the layout is repacked on the
 device in the middle of a step."""
+import os
+
 import numpy as np
 import pytest
 
@@ -98,6 +100,42 @@ def test_layouts_bitwise_equal_other_geometries(case):
     d = run(p, mask, 37, "dense", **init)
     s = run(p, mask, 37, "sparse", **init)
     same(d, s)
+
+
+def run_lists(p, mask, steps, layout, local, **init):
+    old = os.environ.get("LBRBC_LOCAL_LISTS")
+    os.environ["LBRBC_LOCAL_LISTS"] = "1" if local else "0"
+    try:
+        return run(p, mask, steps, layout, **init)
+    finally:
+        if old is None:
+            del os.environ["LBRBC_LOCAL_LISTS"]
+        else:
+            os.environ["LBRBC_LOCAL_LISTS"] = old
+
+
+@pytest.mark.parametrize("layout", ["dense", "sparse"])
+@pytest.mark.parametrize("kind", ["precipitation", "dissolution"])
+def test_local_list_maintenance_matches_full_rebuild(layout, kind):
+    # After events the classes and lists are updated in the cubes around the
+    # events (entries recomputed in place, dead entries skipped, new ones
+    # appended in cell order) instead of over the whole grid: every field,
+    # class and event must be the same bit for bit; the ledger sums the same
+    # terms in another list order.
+    if kind == "precipitation":
+        p, mask, init = pack_case("fp64", 3.0, 1.0, 1.0)
+    else:
+        p, mask, init = pack_case("fp64", 0.0, 1.0, 0.05)
+    steps = 61
+    full = run_lists(p, mask, steps, layout, False, **init)
+    loc = run_lists(p, mask, steps, layout, True, **init)
+    assert len(full["events"]) > 20
+    for x, y in zip(full["fields"], loc["fields"]):
+        assert np.array_equal(x, y)
+    assert np.array_equal(full["classes"], loc["classes"])
+    assert np.array_equal(by_step(full["events"]), by_step(loc["events"]))
+    for k in ("solute", "solid_over_vm", "unpaid", "dirichlet_in", "reacted"):
+        assert loc["ledger"][k] == pytest.approx(full["ledger"][k], rel=1e-13, abs=1e-15), k
 
 
 def test_repacking_matches_oracle():

@@ -572,6 +572,8 @@ def main():
     os.environ["LBRBC_FLUID_SWEEP"] = a.sweep
     K, W = max(1, a.steps), max(3, a.warmup)
     stream = torch.cuda.current_stream()
+    if p.get("phase_change"):
+        p = dict(p, event_log_capacity=1 << 22)  # to count the steps with events
     sim = lbrbc.Sim(p, mask, **extra)
     info = sim.info()
     lay = sim.layout_info()
@@ -584,6 +586,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    nev0 = len(sim.events()) if p.get("phase_change") else 0
     clocks = Clocks(local)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -593,13 +596,18 @@ def main():
     barrier()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
+    # launches in the timed region: every step's, plus the phase-change path
+    # of each step that raised events (a conditional node of the step graphs)
+    lc = sim.launch_counts()
+    ev_steps = len(set(np.asarray(sim.events())[nev0:, 0].tolist())) if p.get("phase_change") else 0
+    launches_timed = lc["per_step"] * K + lc["per_event_step"] * ev_steps
     ms_max, units, per_ms = aggregate(ms, fluid * K, dist, device="cuda")
     value = per_ms * 1e3 / 1e6  # fluid-cell updates per second / 1e6
     sim.check()
 
     # per-kernel durations, CUDA events on the launching stream (no graphs)
     nprof = min(K, 2000)
-    kms, launches = sim.profile(nprof, stream=stream.cuda_stream)
+    kms, _ = sim.profile(nprof, stream=stream.cuda_stream)
     sim.check()
     bytes_launch = BYTES_PER_FLUID_CELL[a.precision] * fluid
     peak, peak_kind = measured_peak()
@@ -710,7 +718,8 @@ def main():
             "roofline": roofline,
             "kernel_ms_per_step": {"fluid": kms[0], "boundary": kms[1], "fluid_ends": kms[2],
                                    "phase_change": kms[3]},
-            "gpu_launches": int(launches * K),
+            "gpu_launches": int(launches_timed),
+            "event_steps_timed": ev_steps,
             "clocks": ck,
             "accuracy": acc,
             "e2e": e2e,

@@ -236,8 +236,16 @@ lbrbc_status lbrbc_adjoint(lbrbc_sim *sim, int64_t n_steps, double *J, double *d
 lbrbc_status lbrbc_profile_step(lbrbc_sim *sim, int64_t n, void *stream, double *ms_out, int64_t *launches);
 
 /* out[0] fluid cells, out[1] wet boundary cells at creation, out[2] kernel
- * launches per time step (host memory, 3 entries). */
+ * launches of a time step without phase-change events (host memory, 3
+ * entries). */
 lbrbc_status lbrbc_info(lbrbc_sim *sim, int64_t *out);
+
+/* Kernel launches of lbrbc_step (host memory, 2 entries): out[0] per time
+ * step without phase-change events, out[1] added by a step with events (the
+ * phase-change path of Sec. 2.4: events, reclassification, list updates;
+ * inside the step graphs it is a conditional node that runs only when the
+ * step raised events).  No GPU work, no synchronisation. */
+lbrbc_status lbrbc_launch_counts(lbrbc_sim *sim, int64_t *out);
 
 /* Population storage of the simulation (host memory, 4 entries): out[0]
  * LBRBC_LAYOUT_DENSE or LBRBC_LAYOUT_SPARSE, out[1] cells holding

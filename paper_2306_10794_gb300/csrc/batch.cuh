@@ -16,6 +16,17 @@
 
 namespace lbrbc {
 
+// Resident blocks per SM the batched active-cell sweep is compiled for
+// (FP32, even and odd steps): the register cap that lets them reside.  The
+// domain's parameters live in registers here (in the single-domain sweep
+// they are constant-bank operands), so the even step needs about 124.
+#ifndef LBRBC_KB_SP_BLOCKS_EVEN
+#define LBRBC_KB_SP_BLOCKS_EVEN 1
+#endif
+#ifndef LBRBC_KB_SP_BLOCKS_ODD
+#define LBRBC_KB_SP_BLOCKS_ODD 1
+#endif
+
 template <typename T>
 struct DomainDesc {
     Dev<T> a;
@@ -59,7 +70,7 @@ __global__ void __launch_bounds__(FLUID_BLOCK) kb_fluid_list4(const DomainDesc<T
 // Active-cell chunk: FLUID_BLOCK consecutive stored cells of one domain on
 // the active-cell layout.  x: domain, y: chunk.
 template <typename T, class LF, class LG, bool ODD>
-__global__ void __launch_bounds__(FLUID_BLOCK) kb_fluid_sp(const DomainDesc<T>* __restrict__ dd,
+__global__ void __launch_bounds__(FLUID_BLOCK, sizeof(T) == 4 ? (ODD ? LBRBC_KB_SP_BLOCKS_ODD : LBRBC_KB_SP_BLOCKS_EVEN) : 4) kb_fluid_sp(const DomainDesc<T>* __restrict__ dd,
                                                         const int2* __restrict__ chunks, int nchunks) {
     for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
         const int2 ch = chunks[c];

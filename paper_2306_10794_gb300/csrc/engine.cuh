@@ -183,13 +183,13 @@ struct Dev {
     uint64_t* b_xyz;      // packed cell coordinates (21 bits each)
     T* b_kappa;           // (QG-1) * cap_b
     double* b_krate;      // cap_b or null
-    int* b_fslot;         // (QG-1) * cap_b: slot in f_share of the fluid end of link o, or -1
+    T* b_share;           // (QG-1) * cap_b: precipitation share of link o (written by k_bound, list order)
     int* bmap;            // NP
     // fluid cells receiving precipitation shares
     int cap_f;
     int* nf;
     int* f_idx;
-    T* f_share;           // (QG-1) * cap_f: share received from the boundary cell at x - e_o
+    int* f_src;           // (QG-1) * cap_f: index in b_share of the share from the boundary cell at x - e_o, or -1
     // compacted fluid cells (packed x | y << 11 | z << 22), when the sweep
     // runs over a list instead of the dense grid
     int use_fl;
@@ -1011,11 +1011,10 @@ __device__ __forceinline__ void bound_entry(const Dev<T>& a, const Phys& p, cons
         a.phi[b] = ph;
     }
     const T r = (sg < 0 && S > T(0)) ? q.neg_vm * T(ms.approx()) / S : T(0);
+    // shares in list order (coalesced); each fluid end gathers its own
 #pragma unroll
-    for (int o = 1; o < Q; ++o) {
-        const int slot = a.b_fslot[(long long)(o - 1) * a.cap_b + e];
-        if (slot >= 0) a.f_share[slot] = r * mabs[o];
-    }
+    for (int o = 1; o < Q; ++o)
+        if ((bw >> (BW_LINK + o - 1)) & 1u) a.b_share[(long long)(o - 1) * a.cap_b + e] = r * mabs[o];
     if (p.phase_change && dle0(ph)) push_event(a.nev, a.cap_e, a.ev_node, a.ev_kind, a.err, (int)b, EV_DISSOLVE);
 }
 
@@ -1059,7 +1058,10 @@ __device__ __forceinline__ void fend_entry(const Dev<T>& a, const Phys& p, int e
     if (f < 0) return;  // no longer a fluid end
     T acc = T(0);
 #pragma unroll
-    for (int o = 1; o < LG::Q; ++o) acc += a.f_share[(long long)(o - 1) * a.cap_f + e];
+    for (int o = 1; o < LG::Q; ++o) {
+        const int s = a.f_src[(long long)(o - 1) * a.cap_f + e];
+        if (s >= 0) acc += a.b_share[s];
+    }
     double ph = a.phi[f];
     if (acc != T(0)) {
         ph += (double)acc;
@@ -1635,51 +1637,36 @@ __global__ void k_loc_append(const Dev<T> a, const Phys p) {
             a.f_idx[pos] = id;
             a.fmap[id] = pos;
 #pragma unroll
-            for (int o = 1; o < LG::Q; ++o) a.f_share[(long long)(o - 1) * a.cap_f + pos] = T(0);
+            for (int o = 1; o < LG::Q; ++o) a.f_src[(long long)(o - 1) * a.cap_f + pos] = -1;
         }
     }
 }
 
-// Share slots of the boundary entries of the region: link o of a reactive
-// wet boundary cell feeds the fluid end downstream of it.  A fluid end of the
-// region clears the shares of links whose source is gone (nothing writes
-// them any more).  Entries outside the region keep their slots: neither end
-// of their links changed.
+// Share sources of the fluid ends of the region: link o gathers from the
+// reactive wet boundary cell at x - e_o.  Fluid ends outside the region keep
+// theirs: a source entry moves only when it is appended or dies, both within
+// one cell of an event, and its fluid ends then lie in the region.
 template <typename T, class LG>
-__global__ void k_loc_fslot(const Dev<T> a) {
+__global__ void k_loc_fsrc(const Dev<T> a) {
     if (!a.lcnt[LC_LOCAL] || a.lcnt[LC_FULL]) return;
     const Geo& g = a.geo;
     const int n = a.lcnt[LC_NREG];
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
         const long long id = a.rlist[r];
+        const int pf = a.fmap[id];
+        if (pf < 0) continue;
         int x, y, z;
         coords(g, id, x, y, z);
-        const int pf = a.fmap[id];
-        if (pf >= 0) {
-#pragma unroll
-            for (int o = 1; o < LG::Q; ++o) {
-                int xs = x - LG::cx(o), ys = y - LG::cy(o), zs = z - LG::cz(o);
-                bool src = false;
-                if (wrap_inside(g, xs, ys, zs)) {
-                    const long long nb = g.idx(xs, ys, zs);
-                    src = (a.nw[nb] & 3u) == CLS_BOUND && a.kind[nb] == KIND_REACTIVE;
-                }
-                if (!src) a.f_share[(long long)(o - 1) * a.cap_f + pf] = T(0);
-            }
-        }
-        const int pb = a.bmap[id];
-        if (pb < 0) continue;
-        const bool reactive = a.kind[id] == KIND_REACTIVE;
 #pragma unroll
         for (int o = 1; o < LG::Q; ++o) {
-            int xf = x + LG::cx(o), yf = y + LG::cy(o), zf = z + LG::cz(o);
-            int slot = -1;
-            if (reactive && wrap_inside(g, xf, yf, zf)) {
-                const long long f = g.idx(xf, yf, zf);
-                const int pf = (a.nw[f] & 3u) == CLS_FLUID ? a.fmap[f] : -1;
-                if (pf >= 0) slot = (o - 1) * a.cap_f + pf;
+            int xs = x - LG::cx(o), ys = y - LG::cy(o), zs = z - LG::cz(o);
+            int src = -1;
+            if (wrap_inside(g, xs, ys, zs)) {
+                const long long nb = g.idx(xs, ys, zs);
+                const int pb = a.bmap[nb];
+                if (pb >= 0 && (a.nw[nb] & 3u) == CLS_BOUND && a.kind[nb] == KIND_REACTIVE) src = (o - 1) * a.cap_b + pb;
             }
-            a.b_fslot[(long long)(o - 1) * a.cap_b + pb] = slot;
+            a.f_src[(long long)(o - 1) * a.cap_f + pf] = src;
         }
     }
 }
@@ -1815,8 +1802,6 @@ __global__ void k_write_lists(const Dev<T> a, const Phys p, int which, int force
             if (which == 0 && pos < a.cap_b) {
                 a.bmap[id] = pos;
                 bound_entry_data<T, LG>(a, p, x, y, z, id, pos);
-#pragma unroll
-                for (int o = 1; o < LG::Q; ++o) a.b_fslot[(long long)(o - 1) * a.cap_b + pos] = -1;
             } else if (which == 2 && pos < a.cap_fl) {
                 a.fl_xyz[pos] = (uint32_t)x | ((uint32_t)y << 11) | ((uint32_t)z << 22);
             } else if (which == 1 && pos < a.cap_f) {
@@ -1824,9 +1809,7 @@ __global__ void k_write_lists(const Dev<T> a, const Phys p, int which, int force
                 if (a.fmap) a.fmap[id] = pos;
 #pragma unroll
                 for (int o = 1; o < LG::Q; ++o) {
-                    const long long slot = (long long)(o - 1) * a.cap_f + pos;
-                    a.f_share[slot] = T(0);
-                    if (src[o] >= 0) a.b_fslot[(long long)(o - 1) * a.cap_b + src[o]] = (int)slot;
+                    a.f_src[(long long)(o - 1) * a.cap_f + pos] = src[o] >= 0 ? (o - 1) * a.cap_b + src[o] : -1;
                 }
             }
         }
@@ -2216,6 +2199,12 @@ template <typename T>
 __global__ void k_ev_reset(const Dev<T> a) {
     const int n = min(*a.nev, a.cap_e);
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) a.evidx[a.ev_node[e]] = -1;
+}
+
+// Condition of the graph node that holds the step's phase-change path.
+template <typename T>
+__global__ void k_ev_gate(const Dev<T> a, cudaGraphConditionalHandle h) {
+    cudaGraphSetConditional(h, *a.nev > 0 ? 1u : 0u);
 }
 
 template <typename T>

@@ -132,6 +132,11 @@ class Engine final : public ISim {
         };
         d_.cap_b = grow(nb0);
         d_.cap_f = grow(nf0);
+        // the share sources index the (QG - 1) x cap_b share array with an int
+        if ((long long)(LG::Q - 1) * std::max(d_.cap_b, d_.cap_f) >= (1LL << 31)) {
+            err = "grid too large: boundary-list capacity exceeds the 32-bit share index";
+            return 1;
+        }
         d_.cap_e = (int)std::min<long long>(ncell_ + 64, std::max<long long>(1 << 16, ncell_ / 64));
         // Sweep over the dense grid (default), over a compacted fluid-cell
         // list (LBRBC_FLUID_SWEEP=list, or a batch schedule).  Measured on
@@ -196,6 +201,10 @@ class Engine final : public ISim {
                 LB_CUDA(dalloc(&d_.cmap2, (size_t)NP));
             }
         }
+        {
+            const char* env = getenv("LBRBC_COND_GRAPH");
+            cond_graphs_ = !(env && !strcmp(env, "0"));
+        }
         // local maintenance of classes and lists after events (default on;
         // LBRBC_LOCAL_LISTS=0 reclassifies the whole grid and compacts the
         // lists in every step with events)
@@ -225,12 +234,13 @@ class Engine final : public ISim {
         LB_CUDA(dalloc(&d_.b_word, (size_t)d_.cap_b));
         LB_CUDA(dalloc(&d_.b_xyz, (size_t)d_.cap_b));
         LB_CUDA(dalloc(&d_.b_kappa, (size_t)(QG - 1) * d_.cap_b));
-        LB_CUDA(dalloc(&d_.b_fslot, (size_t)(QG - 1) * d_.cap_b));
+        LB_CUDA(dalloc(&d_.b_share, (size_t)(QG - 1) * d_.cap_b));
+        LB_CUDA(cudaMemset(d_.b_share, 0, (size_t)(QG - 1) * d_.cap_b * sizeof(T)));
         if (d_.sparse) LB_CUDA(dalloc(&d_.b_cn, (size_t)d_.cap_b));
         LB_CUDA(dalloc(&d_.bmap, (size_t)NP));
         LB_CUDA(dalloc(&d_.nf, 1));
         LB_CUDA(dalloc(&d_.f_idx, (size_t)d_.cap_f));
-        LB_CUDA(dalloc(&d_.f_share, (size_t)(QG - 1) * d_.cap_f));
+        LB_CUDA(dalloc(&d_.f_src, (size_t)(QG - 1) * d_.cap_f));
         LB_CUDA(dalloc(&d_.nfl, 1));
         if (d_.use_fl) LB_CUDA(dalloc(&d_.fl_xyz, (size_t)d_.cap_fl));
         else d_.fl_xyz = nullptr;
@@ -938,47 +948,97 @@ class Engine final : public ISim {
             LB_CUDA(cudaEventRecord(ev[3], st));
         }
         if (ph_.phase_change) {
-            const int eg = 152 * 2;
-            // The event kernels read and write post-collision populations.
-            // Dense layout: at their AA positions after this step.  Active-
-            // cell layout: in the even-step form (each cell's own slots);
-            // after an odd step the links of the event region are swapped
-            // into that form first, and back once the classes have changed.
-            const int form = sp ? 0 : (odd ? 1 : 0);
-            k_ev_mark<T><<<eg, 256, 0, st>>>(d_);
-            if (sp && odd) {
-                k_sp_rmark<T, LG><<<eg, 256, 0, st>>>(d_);
-                k_sp_swap<T, LF, LG><<<eg, 256, 0, st>>>(d_);
+            // Inside a graph the event path is the body of a conditional node
+            // that runs only when this step raised events; a step without
+            // events pays one gate kernel instead of the path's launches.
+            cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+            LB_CUDA(cudaStreamIsCapturing(st, &cst));
+            if (cst == cudaStreamCaptureStatusActive && cond_graphs_) {
+                if (enqueue_events_conditional(st, odd, d_, err)) return 2;
+            } else {
+                enqueue_events(st, odd, d_);
             }
-            k_ev_compute<T, LF, LG><<<eg, 256, 0, st>>>(d_, ph_, form);
-            k_ev_apply_self<T, LF, LG><<<eg, 256, 0, st>>>(d_, ph_, form);
-            k_ev_neighbours<T, LG><<<eg, 256, 0, st>>>(d_, ph_, form);
-            // Classes and lists: locally around the events (the cube of half
-            // width 2 around each), or over the whole grid when the events
-            // are many, the stored set was repacked or the lists need a
-            // compaction.
-            const bool loc = d_.lcnt != nullptr;
-            if (loc) k_loc_decide<T><<<1, 1, 0, st>>>(d_);
-            enqueue_reclassify(st, form, 0);
-            if (loc) k_loc_recl<T, LF, LG><<<eg, 256, 0, st>>>(d_, ph_, form);
-            if (sp) enqueue_repack(st);
-            if (sp) k_sp_retab<T, LF, LG><<<eg, 256, 0, st>>>(d_);
-            if (sp && odd) {
-                k_sp_swap<T, LF, LG><<<eg, 256, 0, st>>>(d_);
-                k_sp_rreset<T, LG><<<eg, 256, 0, st>>>(d_);
-            }
-            if (loc) {
-                k_loc_lists<T, LG><<<eg, 256, 0, st>>>(d_, ph_);
-                k_loc_plan<T><<<1, 1, 0, st>>>(d_);
-                k_loc_append<T, LG><<<eg, 256, 0, st>>>(d_, ph_);
-                k_loc_fslot<T, LG><<<eg, 256, 0, st>>>(d_);
-            }
-            enqueue_lists(st, 0);
-            k_ev_reset<T><<<eg, 256, 0, st>>>(d_);
             k_step_end<T><<<1, 1, 0, st>>>(d_);
         }
         if (ev) LB_CUDA(cudaEventRecord(ev[4], st));
         LB_CUDA(cudaGetLastError());
+        return 0;
+    }
+
+    // The phase-change path of one step: events, classes, stored set, lists.
+    void enqueue_events(cudaStream_t st, bool odd, const Dev<T>& d_) {
+        const bool sp = d_.sparse != 0;
+        const int eg = 152 * 2;
+        // The event kernels read and write post-collision populations.
+        // Dense layout: at their AA positions after this step.  Active-
+        // cell layout: in the even-step form (each cell's own slots);
+        // after an odd step the links of the event region are swapped
+        // into that form first, and back once the classes have changed.
+        const int form = sp ? 0 : (odd ? 1 : 0);
+        k_ev_mark<T><<<eg, 256, 0, st>>>(d_);
+        if (sp && odd) {
+            k_sp_rmark<T, LG><<<eg, 256, 0, st>>>(d_);
+            k_sp_swap<T, LF, LG><<<eg, 256, 0, st>>>(d_);
+        }
+        k_ev_compute<T, LF, LG><<<eg, 256, 0, st>>>(d_, ph_, form);
+        k_ev_apply_self<T, LF, LG><<<eg, 256, 0, st>>>(d_, ph_, form);
+        k_ev_neighbours<T, LG><<<eg, 256, 0, st>>>(d_, ph_, form);
+        // Classes and lists: locally around the events (the cube of half
+        // width 2 around each), or over the whole grid when the events
+        // are many, the stored set was repacked or the lists need a
+        // compaction.
+        const bool loc = d_.lcnt != nullptr;
+        if (loc) k_loc_decide<T><<<1, 1, 0, st>>>(d_);
+        enqueue_reclassify(st, form, 0);
+        if (loc) k_loc_recl<T, LF, LG><<<eg, 256, 0, st>>>(d_, ph_, form);
+        if (sp) enqueue_repack(st);
+        if (sp) k_sp_retab<T, LF, LG><<<eg, 256, 0, st>>>(d_);
+        if (sp && odd) {
+            k_sp_swap<T, LF, LG><<<eg, 256, 0, st>>>(d_);
+            k_sp_rreset<T, LG><<<eg, 256, 0, st>>>(d_);
+        }
+        if (loc) {
+            k_loc_lists<T, LG><<<eg, 256, 0, st>>>(d_, ph_);
+            k_loc_plan<T><<<1, 1, 0, st>>>(d_);
+            k_loc_append<T, LG><<<eg, 256, 0, st>>>(d_, ph_);
+            k_loc_fsrc<T, LG><<<eg, 256, 0, st>>>(d_);
+        }
+        enqueue_lists(st, 0);
+        k_ev_reset<T><<<eg, 256, 0, st>>>(d_);
+    }
+
+    // The same path as the body of an IF node of the graph being captured
+    // on st, gated on the step's event count.
+    int enqueue_events_conditional(cudaStream_t st, bool odd, const Dev<T>& d_, std::string& err) {
+        cudaStreamCaptureStatus cst;
+        cudaGraph_t gr = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        LB_CUDA(cudaStreamGetCaptureInfo(st, &cst, nullptr, &gr, &deps, nullptr, &nd));
+        cudaGraphConditionalHandle h;
+        LB_CUDA(cudaGraphConditionalHandleCreate(&h, gr, 0, 0));
+        k_ev_gate<T><<<1, 1, 0, st>>>(d_, h);
+        LB_CUDA(cudaGetLastError());
+        LB_CUDA(cudaStreamGetCaptureInfo(st, &cst, nullptr, &gr, &deps, nullptr, &nd));
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeIf;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        LB_CUDA(cudaGraphAddNode(&node, gr, deps, nullptr, nd, &np));
+        LB_CUDA(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+        if (!body_) LB_CUDA(cudaStreamCreateWithFlags(&body_, cudaStreamNonBlocking));
+        LB_CUDA(cudaStreamBeginCaptureToGraph(body_, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal));
+        enqueue_events(body_, odd, d_);
+        cudaGraph_t bg = nullptr;
+        const cudaError_t e1 = cudaGetLastError();
+        const cudaError_t e2 = cudaStreamEndCapture(body_, &bg);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) {
+            err = std::string("capture of the event path: ") + cudaGetErrorString(e1 != cudaSuccess ? e1 : e2);
+            return 2;
+        }
         return 0;
     }
 
@@ -993,14 +1053,24 @@ class Engine final : public ISim {
     }
 
    public:
-    // Number of kernel launches of one step (mean of an even and an odd step).
+    // Kernel launches of the phase-change path of one step (mean of an even
+    // and an odd step).
+    int event_path_launches() const override {
+        if (!ph_.phase_change) return 0;
+        int n = 4 + 1 + 3 * (d_.use_fl ? 3 : 2) + 1;       // events, reclassification, lists, reset
+        if (d_.sparse) n += 1 + (1 + 9 + 1) + 6 + 1 + 2;  // repacking (conditional), table refresh, swaps of odd steps / 2
+        if (d_.lcnt) n += 6;                              // local reclassification and list maintenance
+        return n;
+    }
+
+    // Kernel launches of one step of the step graphs without phase-change
+    // events: the fluid sweep, the boundary list and the fluid ends, and with
+    // phase change the gate of the event path and the step counter (the path
+    // itself runs only in steps with events, or always without conditional
+    // graph nodes).
     int launches_per_step() const override {
         int n = 3;
-        if (ph_.phase_change) {
-            n += 4 + 1 + 3 * (d_.use_fl ? 3 : 2) + 2;  // events, reclassification, lists, reset + step end
-            if (d_.sparse) n += 1 + (1 + 9 + 1) + 6 + 1 + 2;  // repacking (conditional), table refresh, swaps of odd steps / 2
-            if (d_.lcnt) n += 6;                              // local reclassification and list maintenance
-        }
+        if (ph_.phase_change) n += cond_graphs_ ? 2 : 1 + event_path_launches();
         return n;
     }
 
@@ -1099,6 +1169,8 @@ class Engine final : public ISim {
         own_ = nullptr;
         if (aux_) cudaStreamDestroy(aux_);
         aux_ = nullptr;
+        if (body_) cudaStreamDestroy(body_);
+        body_ = nullptr;
         if (fork_) cudaEventDestroy(fork_);
         if (join_) cudaEventDestroy(join_);
         fork_ = join_ = nullptr;
@@ -1115,6 +1187,8 @@ class Engine final : public ISim {
     int64_t steps_ = 0;
     cudaStream_t own_ = nullptr, last_stream_ = nullptr, aux_ = nullptr;
     cudaEvent_t fork_ = nullptr, join_ = nullptr;
+    cudaStream_t body_ = nullptr;   // capture stream of the conditional event path
+    bool cond_graphs_ = true;       // LBRBC_COND_GRAPH=0: the event path always runs (early exits)
     int sweep_ = SWEEP_DENSE;
     cudaGraphExec_t g_even_{}, g_odd_{}, g_pair_{};
     bool graphs_ = false;

@@ -165,6 +165,13 @@ lbrbc_status lbrbc_info(lbrbc_sim* sim, int64_t* out) {
     return LBRBC_OK;
 }
 
+lbrbc_status lbrbc_launch_counts(lbrbc_sim* sim, int64_t* out) {
+    if (!sim || !out) return fail(sim, LBRBC_ERR_ARG, "NULL argument");
+    out[0] = sim->impl->launches_per_step();
+    out[1] = sim->impl->event_path_launches();
+    return LBRBC_OK;
+}
+
 lbrbc_status lbrbc_layout_info(lbrbc_sim* sim, int64_t* out) {
     if (!sim || !out) return fail(sim, LBRBC_ERR_ARG, "NULL argument");
     std::string err;

@@ -130,7 +130,7 @@ __device__ __forceinline__ void pair_out(T (&a)[L::Q], int k, int k1, T P0, T P1
 // Flow cell: moments (rho, u) and collision of the flow populations.
 // Equilibrium deviation of direction i: w_i (drho + rho (3 e.u + 4.5 (e.u)^2
 // - 1.5 u.u)); E_k = w_k (drho + rho (4.5 (e.u)^2 - 1.5 u.u)),
-// O_k = 3 w_k rho e_k.u.
+// O_k = 3 w_k rho e_k.u = 3 w_k e_k.j.
 template <class L, typename T>
 __device__ __forceinline__ void flow_pairs(T (&f)[L::Q], T& rho, T& ux, T& uy, T& uz, const Phys& p,
                                            const PhysT<T>& q) {
@@ -159,9 +159,11 @@ __device__ __forceinline__ void flow_pairs(T (&f)[L::Q], T& rho, T& ux, T& uy, T
     for (int k = 1; k <= H; k += 2) {
         const int k1 = k + 1 <= H ? k + 1 : k;
         const T e0 = edot<L, T>(k, ux, uy, uz), e1 = edot<L, T>(k1, ux, uy, uz);
+        const T j0 = edot<L, T>(k, jx, jy, jz), j1 = edot<L, T>(k1, jx, jy, jz);
         const T sw0 = s * T(L::w(k)), sw1 = s * T(L::w(k1));
         const T aw0 = a * mom_coef<L, T>(k), aw1 = a * mom_coef<L, T>(k1);
-        // t = 4.5 (e.u)^2 - 1.5 u.u;  E' = s E = s w (drho + rho t);  O' = a O = a (w / cs^2) rho e.u
+        // t = 4.5 (e.u)^2 - 1.5 u.u;  E' = s E = s w (drho + rho t);  O' = a O = a (w / cs^2) e.j
+        // (rho u = j: the momentum enters without the rounding of u = j / rho)
         T h0, h1, t0, t1, E0, E1, P0, P1, O0, O1, M0, M1;
         mul_x2(T(4.5) * e0, T(4.5) * e1, e0, e1, h0, h1);
         add_x2(h0, h1, m15, m15, t0, t1);
@@ -169,7 +171,7 @@ __device__ __forceinline__ void flow_pairs(T (&f)[L::Q], T& rho, T& ux, T& uy, T
         mul_x2(sw0, sw1, t0, t1, E0, E1);
         esum += k1 != k ? E0 + E1 : E0;
         fma_x2(hs, hs, S[k], S[k + 1], E0, E1, P0, P1);
-        mul_x2(aw0 * rho, aw1 * rho, e0, e1, O0, O1);
+        mul_x2(aw0, aw1, j0, j1, O0, O1);
         fma_x2(ha, ha, D[k], D[k + 1], O0, O1, M0, M1);
         pair_out<L, T>(f, k, k1, P0, P1, M0, M1);
     }

@@ -27,6 +27,7 @@ class ISim {
     virtual int ledger_scratch(double* out, double* scratch, int max_blocks, long long cells_per_block,
                                std::string& err) = 0;
     virtual int launches_per_step() const = 0;
+    virtual int event_path_launches() const = 0;
     virtual int adjoint(int64_t n, double* J, double* dk, double* dceq, double* dk_field, std::string& err) = 0;
     virtual long long fluid_cells() const = 0;
     virtual long long boundary_cells() const = 0;

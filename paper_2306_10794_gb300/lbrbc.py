@@ -56,7 +56,7 @@ _lib = None
 
 EXPORTED = ["lbrbc_create", "lbrbc_step", "lbrbc_fields", "lbrbc_classes", "lbrbc_mass_ledger",
             "lbrbc_mass_ledger_noalloc", "lbrbc_noalloc_size_check",
-            "lbrbc_events", "lbrbc_adjoint", "lbrbc_profile_step", "lbrbc_info", "lbrbc_layout_info", "lbrbc_check", "lbrbc_last_error",
+            "lbrbc_events", "lbrbc_adjoint", "lbrbc_profile_step", "lbrbc_info", "lbrbc_launch_counts", "lbrbc_layout_info", "lbrbc_check", "lbrbc_last_error",
             "lbrbc_destroy", "lbrbc_batch_create", "lbrbc_batch_step", "lbrbc_batch_autotune",
             "lbrbc_batch_info", "lbrbc_batch_domain", "lbrbc_batch_last_error", "lbrbc_batch_destroy"]
 
@@ -97,6 +97,8 @@ def load(path: str = LIB_PATH):
     lib.lbrbc_info.argtypes = [vp, P(ctypes.c_int64)]
     lib.lbrbc_layout_info.restype = ctypes.c_int
     lib.lbrbc_layout_info.argtypes = [vp, P(ctypes.c_int64)]
+    lib.lbrbc_launch_counts.restype = ctypes.c_int
+    lib.lbrbc_launch_counts.argtypes = [vp, P(ctypes.c_int64)]
     lib.lbrbc_check.restype = ctypes.c_int
     lib.lbrbc_check.argtypes = [vp]
     lib.lbrbc_last_error.restype = ctypes.c_char_p
@@ -223,6 +225,13 @@ def lbrbc_info(handle):
     out = (ctypes.c_int64 * 3)()
     _check(lib, handle, lib.lbrbc_info(handle, out))
     return dict(fluid_cells=out[0], boundary_cells=out[1], launches_per_step=out[2])
+
+
+def lbrbc_launch_counts(handle):
+    lib = load()
+    out = (ctypes.c_int64 * 2)()
+    _check(lib, handle, lib.lbrbc_launch_counts(handle, out))
+    return dict(per_step=out[0], per_event_step=out[1])
 
 
 def lbrbc_layout_info(handle):
@@ -372,6 +381,9 @@ class Sim:
 
     def layout_info(self) -> dict:
         return lbrbc_layout_info(self._h)
+
+    def launch_counts(self) -> dict:
+        return lbrbc_launch_counts(self._h)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -19,12 +19,14 @@ namespace lbrbc {
 // Resident blocks per SM the batched active-cell sweep is compiled for
 // (FP32, even and odd steps): the register cap that lets them reside.  The
 // domain's parameters live in registers here (in the single-domain sweep
-// they are constant-bank operands), so the even step needs about 124.
+// they are constant-bank operands): uncapped the even step takes 136
+// registers (3 blocks); capped at 80 it spills 188 B to L1 but measured
+// fastest over 256 domains (2.80 ms per step against 3.26 uncapped).
 #ifndef LBRBC_KB_SP_BLOCKS_EVEN
-#define LBRBC_KB_SP_BLOCKS_EVEN 1
+#define LBRBC_KB_SP_BLOCKS_EVEN 6
 #endif
 #ifndef LBRBC_KB_SP_BLOCKS_ODD
-#define LBRBC_KB_SP_BLOCKS_ODD 1
+#define LBRBC_KB_SP_BLOCKS_ODD 6
 #endif
 
 template <typename T>
@@ -186,8 +188,9 @@ class BatchEngine final : public IBatch {
         {
             std::vector<std::vector<int2>> per(n);
             for (int i = 0; i < n; ++i)
-                if (doms_[i]->sparse())
-                    for (long long c = 0; c * FLUID_BLOCK < doms_[i]->stored0(); ++c) per[i].push_back(make_int2(i, (int)c));
+                if (doms_[i]->sparse())  // the fluid cells are the first range of the stored set
+                    for (long long c = 0; c * FLUID_BLOCK < doms_[i]->fluid_cells(); ++c)
+                        per[i].push_back(make_int2(i, (int)c));
             std::vector<int2> sch;
             // largest domains first, chunks interleaved round-robin
             std::vector<int> idx(n);

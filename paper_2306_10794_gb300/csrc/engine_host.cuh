@@ -820,6 +820,7 @@ class Engine final : public ISim {
 
     void enqueue_reclassify(cudaStream_t st, int form, int force) {
         k_reclassify<T, LF, LG><<<grid_for(ncell_, 256), 256, 0, st>>>(d_, ph_, form, force);
+        k_recl_words<T, LF, LG><<<grid_for(ncell_, 256), 256, 0, st>>>(d_, force);
     }
 
     void enqueue_lists(cudaStream_t st, int force) {
@@ -1057,7 +1058,7 @@ class Engine final : public ISim {
     // and an odd step).
     int event_path_launches() const override {
         if (!ph_.phase_change) return 0;
-        int n = 4 + 1 + 3 * (d_.use_fl ? 3 : 2) + 1;       // events, reclassification, lists, reset
+        int n = 4 + 2 + 3 * (d_.use_fl ? 3 : 2) + 1;       // events, reclassification, lists, reset
         if (d_.sparse) n += 1 + (1 + 9 + 1) + 6 + 1 + 2;  // repacking (conditional), table refresh, swaps of odd steps / 2
         if (d_.lcnt) n += 6;                              // local reclassification and list maintenance
         return n;

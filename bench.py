@@ -41,7 +41,8 @@ ORACLE_MAX_CELLS = 8_000_000
 def args_():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 200; --case adjoint: 4000, the gradient's run length)")
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
@@ -542,6 +543,8 @@ def adjoint_arm(a):
 
 def main():
     a = args_()
+    if a.steps is None:
+        a.steps = 4000 if a.case == "adjoint" else 200
     if a.impl == "reference":
         return reference_arm(a)
     if a.case == "adjoint":

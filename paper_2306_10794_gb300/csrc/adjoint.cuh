@@ -107,6 +107,38 @@ __global__ void __launch_bounds__(LIST_BLOCK, 4) k_adj_bound(const Dev<T> a, con
                 continue;
             }
             const T mo = m[o] + T(1);  // dJ/dh'_o: future through the collision, plus the ledger
+            if constexpr (sizeof(T) == 4) {
+                // FP32 storage: the link terms in FP32 (GB300's FP64 rate is a
+                // small fraction of its FP32 rate), in the deviation form of the
+                // forward rule; each term is added to the FP64 sums once
+                const T kap = a.b_kappa[(long long)(o - 1) * a.cap_b + e];
+                T dkdkr = T(0);
+                bool inf32 = false;
+                if (p.scheme == 0) dkdkr = q.gamma * kap * q.ics2;
+                else if (p.scheme == 1) dkdkr = kap * q.ics2;
+                else if (p.scheme == 2) {
+                    if (kap > T(0)) dkdkr = q.gamma * q.ics2 / kap;
+                    else inf32 = true;
+                } else inf32 = true;
+                if (kr == 0.0) {
+                    out[ob] += mo;
+                    continue;
+                }
+                const T w2 = T(2) * q.gw[o];
+                if (inf32) {
+                    out[ob] += -mo;
+                    gc += (double)(mo * w2);
+                    continue;
+                }
+                const T k = dkdkr * T(kr);
+                const T ik = T(1) / (T(1) + k);
+                out[ob] += (T(1) - k) * ik * mo;
+                // dh'_o/dk = (2 w (c_eq - c_ref) - 2 h_obar') / (1 + k)^2
+                const T dh = (w2 * q.c_eq_d - T(2) * gprev[(long long)(o - 1) * a.cap_b + e]) * ik * ik;
+                cell_k += (double)(mo * dh * dkdkr);
+                gc += (double)(mo * k * ik * w2);
+                continue;
+            }
             const double kap = (double)a.b_kappa[(long long)(o - 1) * a.cap_b + e];
             double dkdkr = 0.0;
             bool inf = false;

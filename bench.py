@@ -480,7 +480,8 @@ def batch_arm(a):
                        "domains": len(cases), "fluid_cells": fluid, "autotune": tune},
             "per_domain_launches": {"ms_per_step": ms_p, "value": fluid / (ms_p * 1e-3) / 1e6, "steps": Kp},
             "batched_speedup": ms_p / ms_b, "clocks": ck,
-            "gpu_launches": 3 * K}
+            # schedule 4 launches every domain's own 3 kernels; the others 3 per step
+            "gpu_launches": 3 * K * (len(cases) if tune["tile_policy"] == 4 else 1)}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -256,11 +256,12 @@ lbrbc_status lbrbc_layout_info(lbrbc_sim *sim, int64_t *out);
 
 /* ---- Batches of independent domains ------------------------------------
  * Many domains of uneven size and their own parameters (same lattices and
- * precision, 3D, no phase change) advanced together: each kernel phase of a
- * step (fluid sweep, wet-boundary list, fluid-end gather) is ONE persistent
- * launch over a schedule of work items from all domains, and step pairs are
- * replayed from a CUDA graph.  Not a construct of the paper: a way to run
- * many of its problems at once. */
+ * precision, 3D, no phase change) advanced together, step pairs replayed
+ * from one CUDA graph: either each kernel phase of a step (fluid sweep,
+ * wet-boundary list, fluid-end gather) is ONE persistent launch over a
+ * schedule of work items from all domains, or (schedule 4) every domain's
+ * own kernels run as independent branches of the graph.  Not a construct of
+ * the paper: a way to run many of its problems at once. */
 typedef struct lbrbc_batch lbrbc_batch; /* opaque, owned by the library */
 
 /* n domains: params[n] (host, copied), masks[n] (host pointers to nx*ny*nz
@@ -272,12 +273,15 @@ lbrbc_status lbrbc_batch_create(int32_t n, const lbrbc_params *params, const uin
 /* Advance every domain by n steps (stream as in lbrbc_step). */
 lbrbc_status lbrbc_batch_step(lbrbc_batch *batch, int64_t n, void *stream);
 
-/* Autotuner: times each candidate schedule (tile width along x 128/64/32 or
- * fitted to the domain, domain-major or largest-first interleaved order,
- * 4/8/16 blocks per SM) for `pairs` step pairs plus one warm-up pair --
- * real steps of every domain -- and keeps the fastest.  choice[3] (host,
- * may be NULL) receives [tile policy, order, blocks per SM]; *ms_per_step
- * (may be NULL) the best time per step in milliseconds. */
+/* Autotuner: times each candidate schedule (persistent kernels: tile width
+ * along x 128/64/32 or fitted to the domain (policies 0-2) or fluid-list
+ * chunks (3), domain-major or largest-first interleaved order, 4/8/16
+ * blocks per SM; or policy 4, the domains' own kernels as parallel graph
+ * branches, 8 x the third entry branch streams: 32/64/128) for `pairs` step
+ * pairs plus one warm-up pair -- real steps of every domain -- and keeps the
+ * fastest.  choice[3] (host, may be NULL) receives [tile policy, order,
+ * blocks per SM]; *ms_per_step (may be NULL) the best time per step in
+ * milliseconds. */
 lbrbc_status lbrbc_batch_autotune(lbrbc_batch *batch, int32_t pairs, void *stream, int64_t *choice,
                                   double *ms_per_step);
 

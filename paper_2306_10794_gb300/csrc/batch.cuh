@@ -248,7 +248,7 @@ class BatchEngine final : public IBatch {
     // domain) and keep the fastest.  choice: [tile policy, order, blocks/SM].
     int autotune(int pairs, cudaStream_t s, int64_t* choice, double* best_ms, std::string& err) override {
         cudaStream_t st = s ? s : own_;
-        const int policies[] = {0, 1, 2, 3}, orders[] = {0, 1}, per_sm[] = {4, 8, 16};
+        const int policies[] = {0, 1, 2, 3, 4}, orders[] = {0, 1}, per_sm[] = {4, 8, 16};
         double best = 1e30;
         int bp = 0, bo = 1, bs = 8;
         cudaEvent_t e0, e1;
@@ -257,6 +257,7 @@ class BatchEngine final : public IBatch {
         for (int pol : policies)
             for (int ord : orders)
                 for (int ps : per_sm) {
+                    if (pol == 4 && ord != 0) continue;  // order does not apply; ps = branches / 4
                     if (set_schedule(pol, ord, ps, err)) return 2;
                     if (step(2, st, err)) return 2;  // warm-up pair
                     LB_BCUDA(cudaEventRecord(e0, st));
@@ -294,7 +295,8 @@ class BatchEngine final : public IBatch {
 
    private:
     // Tile policy 0: width min(128, pow2 >= nx); 1: 64; 2: 32; 3: chunks of
-    // each domain's compacted fluid-cell list instead of dense tiles.  Order
+    // each domain's compacted fluid-cell list instead of dense tiles; 4: no
+    // persistent kernels, the domains' own kernels side by side in one graph.  Order
     // 0: domain by domain; 1: largest domains first with the work items of
     // all domains interleaved round-robin.
     int set_schedule(int policy, int order, int per_sm, std::string& err) {
@@ -303,7 +305,7 @@ class BatchEngine final : public IBatch {
         for (size_t i = 0; i < doms_.size() && policy == 3; ++i)
             if (!doms_[i]->sparse())
                 for (int c = 0; c * FLUID_BLOCK < doms_[i]->host_nfl(); ++c) per[i].push_back(make_int4((int)i, c, 0, 0));
-        for (size_t i = 0; i < doms_.size() && policy != 3; ++i) {
+        for (size_t i = 0; i < doms_.size() && policy < 3; ++i) {
             if (doms_[i]->sparse()) continue;  // its fluid chunks are fixed (sch_)
             const Geo& g = doms_[i]->geo();
             int tw = 128;
@@ -345,6 +347,7 @@ class BatchEngine final : public IBatch {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         grid_ = std::max(1, nsm * per_sm);
+        nbr_ = 8 * per_sm;  // schedule 4: branch streams of the domain graph (32, 64, 128)
         return build_graphs(err);
     }
 
@@ -353,6 +356,7 @@ class BatchEngine final : public IBatch {
     // domain the three touch disjoint population slots, and the gather
     // depends only on the boundary phase.
     int enqueue(cudaStream_t st, bool odd, std::string& err) {
+        if (policy_ == 4) return enqueue_domains(st, odd, err);
         const int gf = std::min(grid_, std::max(1, ntiles_));
         const int gs = std::min(grid_, std::max(1, nsch_));
         const int gb = std::min(grid_, std::max(1, nbch_));
@@ -382,6 +386,48 @@ class BatchEngine final : public IBatch {
         return 0;
     }
 
+    // Schedule 4: every domain's own step kernels (parameters in the launch's
+    // constant bank, the single-domain register budget) as independent
+    // branches of one graph: nbr_ branch streams, the domains dealt largest
+    // first to the branch with the fewest fluid cells so far; each domain's
+    // boundary list forks onto its own second stream.
+    int enqueue_domains(cudaStream_t st, bool odd, std::string& err, bool pair = false) {
+        while ((int)br_.size() < nbr_) {
+            cudaStream_t b;
+            cudaEvent_t e;
+            LB_BCUDA(cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking));
+            LB_BCUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            br_.push_back(b);
+            bj_.push_back(e);
+        }
+        const int nb = std::min<int>(nbr_, (int)doms_.size());
+        std::vector<int> idx(doms_.size()), owner(doms_.size());
+        std::iota(idx.begin(), idx.end(), 0);
+        std::stable_sort(idx.begin(), idx.end(),
+                         [&](int a, int b) { return doms_[a]->fluid_cells() > doms_[b]->fluid_cells(); });
+        std::vector<long long> load(nb, 0);
+        for (int i : idx) {
+            const int j = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            owner[i] = j;
+            load[j] += doms_[i]->fluid_cells() + 1;
+        }
+        LB_BCUDA(cudaEventRecord(fork_, st));
+        for (int j = 0; j < nb; ++j) LB_BCUDA(cudaStreamWaitEvent(br_[j], fork_, 0));
+        // a pair of steps: each domain's second step follows its own first
+        // step on its branch, with no barrier across domains in between
+        for (int i : idx) {
+            if (int rc = doms_[i]->enqueue_own_step(br_[owner[i]], odd, err)) return rc;
+            if (pair)
+                if (int rc = doms_[i]->enqueue_own_step(br_[owner[i]], !odd, err)) return rc;
+        }
+        for (int j = 0; j < nb; ++j) {
+            LB_BCUDA(cudaEventRecord(bj_[j], br_[j]));
+            LB_BCUDA(cudaStreamWaitEvent(st, bj_[j], 0));
+        }
+        LB_BCUDA(cudaGetLastError());
+        return 0;
+    }
+
     int build_graphs(std::string& err) {
         drop_graphs();
         cudaStream_t cs;
@@ -392,6 +438,7 @@ class BatchEngine final : public IBatch {
             int r = 0;
             if (mode == 0) r = enqueue(cs, false, err);
             else if (mode == 1) r = enqueue(cs, true, err);
+            else if (policy_ == 4) r = enqueue_domains(cs, false, err, true);
             else {
                 r = enqueue(cs, false, err);
                 if (!r) r = enqueue(cs, true, err);
@@ -424,6 +471,10 @@ class BatchEngine final : public IBatch {
     void release() {
         if (own_) cudaStreamSynchronize(own_);
         drop_graphs();
+        for (auto b : br_) cudaStreamDestroy(b);
+        for (auto e : bj_) cudaEventDestroy(e);
+        br_.clear();
+        bj_.clear();
         if (dd_) cudaFree(dd_);
         if (tiles_) cudaFree(tiles_);
         if (bch_) cudaFree(bch_);
@@ -451,6 +502,9 @@ class BatchEngine final : public IBatch {
     int lastodd_ = 1;
     cudaStream_t own_ = nullptr, aux_ = nullptr;
     cudaEvent_t fork_ = nullptr, join_ = nullptr;
+    int nbr_ = 32;
+    std::vector<cudaStream_t> br_;  // branch streams of the domain-graph schedule
+    std::vector<cudaEvent_t> bj_;
     cudaGraphExec_t g_even_{}, g_odd_{}, g_pair_{};
     bool graphs_ = false;
 };

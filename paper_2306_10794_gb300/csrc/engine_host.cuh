@@ -545,6 +545,9 @@ class Engine final : public ISim {
     bool uses_list() const { return d_.use_fl != 0; }
     double lane_efficiency() const { return lane_eff_; }
     int host_nfl() const { return (int)nfluid_; }
+    // One step of this domain's own kernels on st (the batched engine's
+    // domain-graph schedule captures these side by side).
+    int enqueue_own_step(cudaStream_t st, bool odd, std::string& err) { return enqueue_step(st, odd, err); }
     // Record n steps taken by the batched kernels (parity after them: lastodd).
     void advance(int64_t n, int lastodd, cudaStream_t st) {
         steps_ += n;

@@ -47,8 +47,10 @@ def test_batch_autotuned_equals_single_domains(precision):
     b = lbrbc.Batch(cases)
     choice = b.autotune(pairs=1)
     assert choice["ms_per_step"] > 0.0
-    # every candidate ran 1 warm-up pair + 1 timed pair
-    n_auto = 4 * 2 * 3 * 4
+    # every candidate ran 1 warm-up pair + 1 timed pair: 4 persistent-kernel
+    # policies x 2 orders x 3 grids, and the domain-graph schedule with 3
+    # branch counts
+    n_auto = (4 * 2 * 3 + 3) * 4
     b.step(5)
     total = n_auto + 5
     for i, (p, mask, init) in enumerate(cases):
@@ -81,11 +83,12 @@ def test_batch_domain_handles_are_borrowed():
 def test_batch_many_small_domains(precision):
     # a hundred-odd small domains: the work items of many domains share every
     # block of the persistent launches, each domain still evolving as it does
-    # alone under every tile policy and order
+    # alone under every tile policy and order and as a branch of the domain
+    # graph
     cases, _ = workloads.case_batch(n=110, L_min=9, L_max=16, seed=11, precision=precision)
     b = lbrbc.Batch(cases)
     choice = b.autotune(pairs=1)
-    total = 4 * 2 * 3 * 4 + 3
+    total = (4 * 2 * 3 + 3) * 4 + 3
     b.step(3)
     for i in range(0, 110, 7):
         p, mask, init = cases[i]

@@ -285,6 +285,12 @@ lbrbc_status lbrbc_batch_step(lbrbc_batch *batch, int64_t n, void *stream);
 lbrbc_status lbrbc_batch_autotune(lbrbc_batch *batch, int32_t pairs, void *stream, int64_t *choice,
                                   double *ms_per_step);
 
+/* Fix the schedule without timing: the three numbers lbrbc_batch_autotune
+ * reports (policy 0-4, order 0-1, blocks per SM 1-64; for policy 4 the
+ * branch streams are 8 x blocks_per_sm).  LBRBC_ERR_ARG when out of range.
+ * Rebuilds the step graphs; call it between steps. */
+lbrbc_status lbrbc_batch_schedule(lbrbc_batch *batch, int32_t policy, int32_t order, int32_t blocks_per_sm);
+
 /* out[0] number of domains, out[1] total fluid cells (host, 2 entries). */
 lbrbc_status lbrbc_batch_info(lbrbc_batch *batch, int64_t *out);
 

@@ -230,7 +230,10 @@ class BatchEngine final : public IBatch {
         cudaStream_t st = s ? s : own_;
         int64_t k = 0;
         while (k < n) {
-            if (!lastodd_ || n - k < 2) {
+            if (multi_ && lastodd_ && n - k >= MSTEP) {
+                LB_BCUDA(cudaGraphLaunch(g_multi_, st));  // MSTEP (even) steps, parity kept
+                k += MSTEP;
+            } else if (!lastodd_ || n - k < 2) {
                 LB_BCUDA(cudaGraphLaunch(lastodd_ ? g_even_ : g_odd_, st));
                 lastodd_ ^= 1;
                 k += 1;
@@ -283,6 +286,10 @@ class BatchEngine final : public IBatch {
         }
         if (best_ms) *best_ms = best / (2.0 * pairs);
         return 0;
+    }
+
+    int schedule(int policy, int order, int per_sm, std::string& err) override {
+        return set_schedule(policy, order, per_sm, err);
     }
 
     int size() const override { return (int)doms_.size(); }
@@ -391,7 +398,8 @@ class BatchEngine final : public IBatch {
     // branches of one graph: nbr_ branch streams, the domains dealt largest
     // first to the branch with the fewest fluid cells so far; each domain's
     // boundary list forks onto its own second stream.
-    int enqueue_domains(cudaStream_t st, bool odd, std::string& err, bool pair = false) {
+    // nsteps steps of every domain, chained per domain on its branch.
+    int enqueue_domains(cudaStream_t st, bool odd, std::string& err, int nsteps = 1) {
         while ((int)br_.size() < nbr_) {
             cudaStream_t b;
             cudaEvent_t e;
@@ -413,13 +421,11 @@ class BatchEngine final : public IBatch {
         }
         LB_BCUDA(cudaEventRecord(fork_, st));
         for (int j = 0; j < nb; ++j) LB_BCUDA(cudaStreamWaitEvent(br_[j], fork_, 0));
-        // a pair of steps: each domain's second step follows its own first
+        // several steps: each domain's next step follows its own previous
         // step on its branch, with no barrier across domains in between
-        for (int i : idx) {
-            if (int rc = doms_[i]->enqueue_own_step(br_[owner[i]], odd, err)) return rc;
-            if (pair)
-                if (int rc = doms_[i]->enqueue_own_step(br_[owner[i]], !odd, err)) return rc;
-        }
+        for (int i : idx)
+            for (int t = 0; t < nsteps; ++t)
+                if (int rc = doms_[i]->enqueue_own_step(br_[owner[i]], (t & 1) ? !odd : odd, err)) return rc;
         for (int j = 0; j < nb; ++j) {
             LB_BCUDA(cudaEventRecord(bj_[j], br_[j]));
             LB_BCUDA(cudaStreamWaitEvent(st, bj_[j], 0));
@@ -438,7 +444,7 @@ class BatchEngine final : public IBatch {
             int r = 0;
             if (mode == 0) r = enqueue(cs, false, err);
             else if (mode == 1) r = enqueue(cs, true, err);
-            else if (policy_ == 4) r = enqueue_domains(cs, false, err, true);
+            else if (policy_ == 4) r = enqueue_domains(cs, false, err, mode == 2 ? 2 : MSTEP);
             else {
                 r = enqueue(cs, false, err);
                 if (!r) r = enqueue(cs, true, err);
@@ -453,7 +459,12 @@ class BatchEngine final : public IBatch {
             cudaGraphDestroy(gr);
             return 0;
         };
-        const int r = cap(&g_even_, 0) || cap(&g_odd_, 1) || cap(&g_pair_, 2);
+        int r = cap(&g_even_, 0) || cap(&g_odd_, 1) || cap(&g_pair_, 2);
+        multi_ = false;
+        if (!r && policy_ == 4) {
+            r = cap(&g_multi_, 3);
+            multi_ = r == 0;
+        }
         cudaStreamDestroy(cs);
         if (r) return 2;
         graphs_ = true;
@@ -465,6 +476,8 @@ class BatchEngine final : public IBatch {
         cudaGraphExecDestroy(g_even_);
         cudaGraphExecDestroy(g_odd_);
         cudaGraphExecDestroy(g_pair_);
+        if (multi_) cudaGraphExecDestroy(g_multi_);
+        multi_ = false;
         graphs_ = false;
     }
 
@@ -506,6 +519,10 @@ class BatchEngine final : public IBatch {
     std::vector<cudaStream_t> br_;  // branch streams of the domain-graph schedule
     std::vector<cudaEvent_t> bj_;
     cudaGraphExec_t g_even_{}, g_odd_{}, g_pair_{};
+    // schedule 4: MSTEP steps per graph launch (fewer joins across domains)
+    static constexpr int MSTEP = 8;
+    cudaGraphExec_t g_multi_{};
+    bool multi_ = false;
     bool graphs_ = false;
 };
 

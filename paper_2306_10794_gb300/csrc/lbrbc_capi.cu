@@ -253,6 +253,15 @@ lbrbc_status lbrbc_batch_autotune(lbrbc_batch* b, int32_t pairs, void* stream, i
     return (lbrbc_status)rc;
 }
 
+lbrbc_status lbrbc_batch_schedule(lbrbc_batch* b, int32_t policy, int32_t order, int32_t blocks_per_sm) {
+    if (!b) return LBRBC_ERR_ARG;
+    if (policy < 0 || policy > 4 || order < 0 || order > 1 || blocks_per_sm < 1 || blocks_per_sm > 64) {
+        b->err = "schedule out of range (policy 0-4, order 0-1, blocks per SM 1-64)";
+        return LBRBC_ERR_ARG;
+    }
+    return (lbrbc_status)b->impl->schedule(policy, order, blocks_per_sm, b->err);
+}
+
 lbrbc_status lbrbc_batch_info(lbrbc_batch* b, int64_t* out) {
     if (!b || !out) return LBRBC_ERR_ARG;
     out[0] = b->impl->size();

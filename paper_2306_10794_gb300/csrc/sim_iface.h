@@ -42,6 +42,7 @@ class IBatch {
                      std::string& err) = 0;
     virtual int step(int64_t n, cudaStream_t s, std::string& err) = 0;
     virtual int autotune(int pairs, cudaStream_t s, int64_t* choice, double* ms_per_step, std::string& err) = 0;
+    virtual int schedule(int policy, int order, int per_sm, std::string& err) = 0;
     virtual int size() const = 0;
     virtual ISim* domain(int i) = 0;
     virtual long long fluid_cells() const = 0;

@@ -57,7 +57,7 @@ _lib = None
 EXPORTED = ["lbrbc_create", "lbrbc_step", "lbrbc_fields", "lbrbc_classes", "lbrbc_mass_ledger",
             "lbrbc_mass_ledger_noalloc", "lbrbc_noalloc_size_check",
             "lbrbc_events", "lbrbc_adjoint", "lbrbc_profile_step", "lbrbc_info", "lbrbc_launch_counts", "lbrbc_layout_info", "lbrbc_check", "lbrbc_last_error",
-            "lbrbc_destroy", "lbrbc_batch_create", "lbrbc_batch_step", "lbrbc_batch_autotune",
+            "lbrbc_destroy", "lbrbc_batch_create", "lbrbc_batch_step", "lbrbc_batch_autotune", "lbrbc_batch_schedule",
             "lbrbc_batch_info", "lbrbc_batch_domain", "lbrbc_batch_last_error", "lbrbc_batch_destroy"]
 
 
@@ -111,6 +111,8 @@ def load(path: str = LIB_PATH):
     lib.lbrbc_batch_step.argtypes = [vp, ctypes.c_int64, vp]
     lib.lbrbc_batch_autotune.restype = ctypes.c_int
     lib.lbrbc_batch_autotune.argtypes = [vp, ctypes.c_int32, vp, P(ctypes.c_int64), dp]
+    lib.lbrbc_batch_schedule.restype = ctypes.c_int
+    lib.lbrbc_batch_schedule.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
     lib.lbrbc_batch_info.restype = ctypes.c_int
     lib.lbrbc_batch_info.argtypes = [vp, P(ctypes.c_int64)]
     lib.lbrbc_batch_domain.restype = vp
@@ -438,6 +440,10 @@ class Batch:
         self._chk(self._lib.lbrbc_batch_autotune(self._h, int(pairs), ctypes.c_void_p(stream) if stream else None,
                                                  ch, ctypes.byref(ms)))
         return dict(tile_policy=ch[0], order=ch[1], blocks_per_sm=ch[2], ms_per_step=ms.value)
+
+    def schedule(self, policy: int, order: int = 0, blocks_per_sm: int = 4):
+        """Fix the schedule (the numbers autotune reports) without timing."""
+        self._chk(self._lib.lbrbc_batch_schedule(self._h, int(policy), int(order), int(blocks_per_sm)))
 
     def info(self):
         out = (ctypes.c_int64 * 2)()

@@ -98,3 +98,22 @@ def test_batch_many_small_domains(precision):
         for a, c in zip(b.fields(i), s.fields()):
             assert np.abs(a - c).max() <= tol * max(1.0, np.abs(c).max()), (i, choice)
         s.close()
+
+
+@pytest.mark.parametrize("schedule", [(0, 0, 4), (2, 1, 8), (3, 1, 16), (4, 0, 4), (4, 0, 16)])
+def test_batch_fixed_schedules_equal_single_domains(schedule):
+    # every schedule, fixed without timing, over 19 steps: the domain-graph
+    # schedule then runs its 8-step graphs twice, a pair and a single step
+    cases = _cases("fp32", n=9)
+    b = lbrbc.Batch(cases)
+    b.schedule(*schedule)
+    b.step(19)
+    for i, (p, mask, init) in enumerate(cases):
+        s = lbrbc.Sim(p, mask, **init)
+        s.step(19)
+        for a, c in zip(b.fields(i), s.fields()):
+            assert np.abs(a - c).max() <= 2e-6 * max(1.0, np.abs(c).max()), (i, schedule)
+        assert lbrbc.lbrbc_mass_ledger(b.domain(i))[5] == 19
+        s.close()
+    with pytest.raises(lbrbc.LbrbcError):
+        b.schedule(5)

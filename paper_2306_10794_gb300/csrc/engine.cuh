@@ -232,8 +232,8 @@ struct Dev {
     int* cmap;            // NP: compact index of a padded cell, -1 if not stored
     int* cid;             // cap_s: padded index of compact cell n
     uint32_t* nwc;        // cap_s: node word of compact cell n
-    uint32_t* etab;       // effective block bases of each stored cell's neighbours (see k_sp_tables),
-                          // blocked by 32 cells: (QF - 1) flow then (QG - 1) solute entries per cell
+    uint32_t* etab;       // neighbour table of each stored cell (see sp_cell_tables), blocked by 32
+                          // cells: QF - 1 entries per cell (QG - 1 without a flow lattice)
     int* b_cn;            // cap_b: compact index of each wet boundary cell
     int* rown;            // NP: owner of a cell of the event region (RNONE outside), event path
     // local maintenance of the classes and lists after phase-change events
@@ -522,23 +522,52 @@ __device__ __forceinline__ size_t etab_at(uint32_t n, int nt, int k) {
     return (size_t)(n & ~31u) * (size_t)nt + (size_t)k * 32u + (n & 31u);
 }
 
+// Table entries per stored cell: one per flow direction (with a flow
+// lattice), else one per solute direction.  A flow direction whose velocity
+// is also a solute velocity ("shared", the 6 axis directions of D3Q19 /
+// D3Q7) holds the compact index of the neighbour when it is not solid (it is
+// then stored), and the reads and writes of both lattices along it test the
+// node word; every other direction holds the folded effective base of its
+// lattice.  One table thus serves both lattices (96 -> 72 B per cell in 3D).
+template <class LF, class LG>
+__host__ __device__ constexpr int tab_entries() {
+    return LF::Q > 0 ? LF::Q - 1 : LG::Q - 1;
+}
+template <class LF, class LG>
+__host__ __device__ constexpr bool shared_dir(int k) {
+    if constexpr (LF::Q == 0) {
+        return false;
+    } else {
+        for (int j = 1; j < LG::Q; ++j)
+            if (LG::cx(j) == LF::cx(k) && LG::cy(j) == LF::cy(k) && LG::cz(j) == LF::cz(k)) return true;
+        return false;
+    }
+}
+
 template <typename T, class LF, class LG, bool ODD>
 struct SparseSrc {
-    static constexpr bool kTargets = false;  // inactive targets are folded into the table
-    static constexpr bool kBranchFree = true;  // no read or write depends on the node word
-    static constexpr int QF1 = LF::Q > 0 ? LF::Q - 1 : 0;
-    static constexpr int NT = QF1 + LG::Q - 1;
+    static constexpr bool kTargets = false;  // inactive targets are handled inside (table or node word)
+    static constexpr bool kBranchFree = true;  // no branch: per-direction selects of addresses
+    static constexpr int NT = tab_entries<LF, LG>();
     const T* __restrict__ F;
     const T* __restrict__ G;
     const uint32_t* __restrict__ et;  // this cell's table entries (entry k at et[32 k])
     uint32_t n;
     T* Fw;
     T* Gw;
+    uint32_t w;  // node word: inactive sources of both lattices
     __device__ __forceinline__ uint32_t e(int k) const { return __ldg(et + 32 * k); }
-    // slot E[k] + 32 d: the sum is formed in 32-bit unsigned arithmetic (an
-    // inactive neighbour's entry wraps around and the sum comes back to the
-    // own slot) before it offsets a pointer
+    // slot E[k] + 32 d of a folded entry: the sum is formed in 32-bit
+    // unsigned arithmetic (an inactive neighbour's entry wraps around and the
+    // sum comes back to the own slot) before it offsets a pointer
     __device__ __forceinline__ uint32_t slot(int k, int d) const { return e(k) + 32u * (uint32_t)d; }
+    // slot of direction d of lattice L in the neighbour of shared flow
+    // direction k, or the own slot `own` when inactive
+    template <class L>
+    __device__ __forceinline__ uint32_t shared(int k, int d, bool inactive, uint32_t own) const {
+        const uint32_t m = e(k);
+        return inactive ? own : pbase<L>(m) + 32u * (uint32_t)d;
+    }
     __device__ __forceinline__ T ld_nbr(const T* p) const {
 #if LBRBC_SP_NBR_HINT
         return ld_pop(p);
@@ -549,12 +578,19 @@ struct SparseSrc {
     __device__ __forceinline__ T f(int i, bool) const {
         if (!ODD || i == 0) return ld_pop(F + pslot<LF>(i, n));
         const int d = LF::opp(i);
+        if (shared_dir<LF, LG>(d))
+            return ld_nbr(F + shared<LF>(d - 1, d, (w >> (FBIT + i - 1)) & 1u, pslot<LF>(i, n)));
         return ld_nbr(F + slot(d - 1, d));
     }
     __device__ __forceinline__ T g(int i, bool) const {
         if (!ODD || i == 0) return ld_pop(G + pslot<LG>(i, n));
         const int d = LG::opp(i);
-        return ld_nbr(G + slot(QF1 + d - 1, d));
+        if constexpr (LF::Q > 0) {
+            const int k = sdir<LF, LG>(d);
+            return ld_nbr(G + shared<LG>(k - 1, d, (w >> (GBIT + i - 1)) & 1u, pslot<LG>(i, n)));
+        } else {
+            return ld_nbr(G + slot(d - 1, d));
+        }
     }
     __device__ __forceinline__ void st_nbr(T* p, T v) const {
 #if LBRBC_SP_NBR_STORE_HINT
@@ -564,12 +600,23 @@ struct SparseSrc {
 #endif
     }
     __device__ __forceinline__ void fput(int i, T v, bool) const {
-        if (!ODD || i == 0) st_pop(Fw + pslot<LF>(LF::opp(i), n), v);
-        else st_nbr(Fw + slot(i - 1, i), v);
+        if (!ODD || i == 0) {
+            st_pop(Fw + pslot<LF>(LF::opp(i), n), v);
+        } else if (shared_dir<LF, LG>(i)) {
+            st_nbr(Fw + shared<LF>(i - 1, i, (w >> (FBIT + LF::opp(i) - 1)) & 1u, pslot<LF>(LF::opp(i), n)), v);
+        } else {
+            st_nbr(Fw + slot(i - 1, i), v);
+        }
     }
     __device__ __forceinline__ void gput(int i, T v, bool) const {
-        if (!ODD || i == 0) st_pop(Gw + pslot<LG>(LG::opp(i), n), v);
-        else st_nbr(Gw + slot(QF1 + i - 1, i), v);
+        if (!ODD || i == 0) {
+            st_pop(Gw + pslot<LG>(LG::opp(i), n), v);
+        } else if constexpr (LF::Q > 0) {
+            const int k = sdir<LF, LG>(i);
+            st_nbr(Gw + shared<LG>(k - 1, i, (w >> (GBIT + LG::opp(i) - 1)) & 1u, pslot<LG>(LG::opp(i), n)), v);
+        } else {
+            st_nbr(Gw + slot(i - 1, i), v);
+        }
     }
 };
 
@@ -720,7 +767,7 @@ __device__ __forceinline__ void sparse_cell(const Dev<T>& a, const Phys& p, cons
         coords(a.geo, id, x, y, z);
     }
     constexpr int NT = SparseSrc<T, LF, LG, ODD>::NT;
-    const SparseSrc<T, LF, LG, ODD> src{a.F, a.G, a.etab + etab_at((uint32_t)n, NT, 0), (uint32_t)n, a.F, a.G};
+    const SparseSrc<T, LF, LG, ODD> src{a.F, a.G, a.etab + etab_at((uint32_t)n, NT, 0), (uint32_t)n, a.F, a.G, w};
     fluid_cell_src<T, LF, LG, ODD>(a, p, q, id, w, src, inlet, outlet, y, z);
 }
 
@@ -888,14 +935,13 @@ __device__ __forceinline__ void unpack_xyz(uint64_t v, int& x, int& y, int& z) {
 // neighbour table; LF only names the table's stencil).
 template <typename T, class LF, class LG, bool ODD, bool SP>
 struct BoundSlots {
-    static constexpr int QF1 = LF::Q > 0 ? LF::Q - 1 : 0;
     Blk<LG> kb;
     uint32_t n;
     const uint32_t* et;
     __device__ __forceinline__ BoundSlots(const Dev<T>& a, int e) {
         if constexpr (SP) {
             n = (uint32_t)a.b_cn[e];
-            et = a.etab + etab_at(n, QF1 + LG::Q - 1, QF1);
+            et = a.etab + etab_at(n, tab_entries<LF, LG>(), 0);
         } else {
             int x, y, z;
             unpack_xyz(a.b_xyz[e], x, y, z);
@@ -903,11 +949,19 @@ struct BoundSlots {
             kb = blk_of<LG>(b, nbr32(a.geo, x, y, z));
         }
     }
+    // (active-cell layout with a flow lattice: the solute directions are
+    // shared table entries holding the neighbour's compact index, selected by
+    // the cell's inactive-source bits; without one, folded solute entries)
     __device__ __forceinline__ uint32_t rd(int i, bool inactive) const {
         if constexpr (SP) {
             if (!ODD || i == 0) return pslot<LG>(i, n);
             const int d = LG::opp(i);
-            return et[32 * (d - 1)] + 32u * (uint32_t)d;
+            if constexpr (LF::Q > 0) {
+                const uint32_t m = et[32 * (sdir<LF, LG>(d) - 1)];
+                return inactive ? pslot<LG>(i, n) : pbase<LG>(m) + 32u * (uint32_t)d;
+            } else {
+                return et[32 * (d - 1)] + 32u * (uint32_t)d;
+            }
         } else {
             return read_slot<LG, ODD>(kb, i, inactive);
         }
@@ -915,7 +969,12 @@ struct BoundSlots {
     __device__ __forceinline__ uint32_t wr(int i, bool inactive) const {
         if constexpr (SP) {
             if (!ODD || i == 0) return pslot<LG>(LG::opp(i), n);
-            return et[32 * (i - 1)] + 32u * (uint32_t)i;
+            if constexpr (LF::Q > 0) {
+                const uint32_t m = et[32 * (sdir<LF, LG>(i) - 1)];
+                return inactive ? pslot<LG>(LG::opp(i), n) : pbase<LG>(m) + 32u * (uint32_t)i;
+            } else {
+                return et[32 * (i - 1)] + 32u * (uint32_t)i;
+            }
         } else {
             return write_slot<LG, ODD>(kb, i);
         }

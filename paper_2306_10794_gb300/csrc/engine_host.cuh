@@ -881,7 +881,7 @@ class Engine final : public ISim {
         LB_CUDA(cudaMemset(d_.G, 0, (size_t)QG * cap * sizeof(T)));
         LB_CUDA(dalloc(&d_.cid, (size_t)cap));
         LB_CUDA(dalloc(&d_.nwc, (size_t)cap));
-        LB_CUDA(dalloc(&d_.etab, (size_t)((LF::Q > 0 ? LF::Q - 1 : 0) + LG::Q - 1) * cap));
+        LB_CUDA(dalloc(&d_.etab, (size_t)tab_entries<LF, LG>() * cap));
         LB_CUDA(cudaMemset(d_.nwc, 0, cap * sizeof(uint32_t)));
         if (prm_.phase_change) {
             LB_CUDA(dalloc(&d_.cid2, (size_t)cap));

@@ -854,14 +854,17 @@ __global__ void k_sp_total(const Dev<T> a, const int* __restrict__ tot, int* __r
     *ns_out = (int)min(n, a.cap_s);
 }
 
-// Node word and effective-base table entries of stored cell n (padded
-// index id): for each neighbour direction d of each lattice, the block base
-// of the neighbour id + e_d when it is active for that lattice (flow: fluid;
-// solute: not solid) -- it is then stored -- else the cell's own base plus
-// 32 (opp(d) - d), so that slot E[d] + 32 d is the own slot opp(d).
+// Node word and table entries of stored cell n (padded index id).  With a
+// flow lattice one entry per flow direction k: for a shared direction (also a
+// solute velocity) the neighbour's compact index when it is not solid (else
+// the cell's own index; the sweep then takes its own slot from the node
+// word), for the others the folded effective base -- the neighbour's block
+// base when it is fluid, else the cell's own base plus 32 (opp(k) - k), so
+// that slot E[k] + 32 k is the own slot opp(k).  Without a flow lattice the
+// folded entries of the solute directions (active: not solid).
 template <typename T, class LF, class LG>
 __device__ __forceinline__ void sp_cell_tables(const Dev<T>& a, uint32_t n, long long id) {
-    constexpr int QF1 = LF::Q > 0 ? LF::Q - 1 : 0, NT = QF1 + LG::Q - 1;
+    constexpr int NT = tab_entries<LF, LG>();
     a.nwc[n] = a.nw[id];
     const Nbr d = nbr_of(a.geo, id);
     if constexpr (LF::Q > 0) {
@@ -869,18 +872,27 @@ __device__ __forceinline__ void sp_cell_tables(const Dev<T>& a, uint32_t n, long
 #pragma unroll
         for (int k = 1; k < LF::Q; ++k) {
             const long long nb = id + off<LF>(d, k);
-            const bool act = (a.nw[nb] & 3u) == CLS_FLUID;
-            a.etab[etab_at(n, NT, k - 1)] =
-                act ? pbase<LF>((uint32_t)a.cmap[nb]) : own + 32u * (uint32_t)(LF::opp(k) - k);
+            const uint32_t cls = a.nw[nb] & 3u;
+            const int cm = a.cmap[nb];
+            // an active neighbour is always stored; should one not be, the
+            // entry points at the cell itself and the run reports an error
+            if (cls != CLS_SOLID && cm < 0) atomicOr(a.err, ERR_OVERFLOW);
+            uint32_t v;
+            if (shared_dir<LF, LG>(k)) v = cls != CLS_SOLID && cm >= 0 ? (uint32_t)cm : n;
+            else v = cls == CLS_FLUID && cm >= 0 ? pbase<LF>((uint32_t)cm) : own + 32u * (uint32_t)(LF::opp(k) - k);
+            a.etab[etab_at(n, NT, k - 1)] = v;
         }
-    }
-    const uint32_t own = pbase<LG>(n);
+    } else {
+        const uint32_t own = pbase<LG>(n);
 #pragma unroll
-    for (int k = 1; k < LG::Q; ++k) {
-        const long long nb = id + off<LG>(d, k);
-        const bool act = (a.nw[nb] & 3u) != CLS_SOLID;
-        a.etab[etab_at(n, NT, QF1 + k - 1)] =
-            act ? pbase<LG>((uint32_t)a.cmap[nb]) : own + 32u * (uint32_t)(LG::opp(k) - k);
+        for (int k = 1; k < LG::Q; ++k) {
+            const long long nb = id + off<LG>(d, k);
+            const int cm = a.cmap[nb];
+            const bool act = (a.nw[nb] & 3u) != CLS_SOLID;
+            if (act && cm < 0) atomicOr(a.err, ERR_OVERFLOW);
+            a.etab[etab_at(n, NT, k - 1)] =
+                act && cm >= 0 ? pbase<LG>((uint32_t)cm) : own + 32u * (uint32_t)(LG::opp(k) - k);
+        }
     }
 }
 

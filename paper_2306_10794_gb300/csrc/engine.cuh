@@ -1070,10 +1070,11 @@ __device__ __forceinline__ void bound_entry(const Dev<T>& a, const Phys& p, cons
         a.phi[b] = ph;
     }
     const T r = (sg < 0 && S > T(0)) ? q.neg_vm * T(ms.approx()) / S : T(0);
-    // shares in list order (coalesced); each fluid end gathers its own
+    // shares in list order; each fluid end gathers its own.  Every direction
+    // is written (0 without a link), so a warp writes whole sectors and the
+    // L2 need not fetch partly written ones from DRAM.
 #pragma unroll
-    for (int o = 1; o < Q; ++o)
-        if ((bw >> (BW_LINK + o - 1)) & 1u) a.b_share[(long long)(o - 1) * a.cap_b + e] = r * mabs[o];
+    for (int o = 1; o < Q; ++o) a.b_share[(long long)(o - 1) * a.cap_b + e] = r * mabs[o];
     if (p.phase_change && dle0(ph)) push_event(a.nev, a.cap_e, a.ev_node, a.ev_kind, a.err, (int)b, EV_DISSOLVE);
 }
 

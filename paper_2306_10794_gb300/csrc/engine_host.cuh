@@ -222,6 +222,11 @@ class Engine final : public ISim {
                 LB_CUDA(dalloc(&d_.lcnt, (size_t)LC_N));
                 LB_CUDA(cudaMemset(d_.lcnt, 0, LC_N * sizeof(int)));
                 LB_CUDA(dalloc(&d_.rlist, (size_t)LOC_EV_MAX * loc_cube<LG::DIM>()));
+                // LBRBC_LOCAL_EV_MAX lowers the limit (tests mix local and
+                // whole-grid steps in small runs)
+                const char* lim = getenv("LBRBC_LOCAL_EV_MAX");
+                const int evmax = lim ? std::max(0, std::min(LOC_EV_MAX, atoi(lim))) : LOC_EV_MAX;
+                LB_CUDA(cudaMemcpy(d_.lcnt + LC_EVMAX, &evmax, sizeof(int), cudaMemcpyHostToDevice));
             }
         }
         LB_CUDA(dalloc(&d_.nw, (size_t)NP));

@@ -268,6 +268,7 @@ enum {
     LC_BASEB = 6,   // list lengths before this step's appends
     LC_BASEF = 7,
     LC_NREG = 8,    // cells of this step's region
+    LC_EVMAX = 9,   // events of a step handled locally (at most LOC_EV_MAX; more: whole grid)
     LC_N = 16
 };
 // Cells that a change of kind at an event cell can affect: a cell's class
@@ -278,7 +279,7 @@ enum {
 // neighbours.  Every such offset lies in the cube of half width 2.
 constexpr int LOC_HALF = 2;
 constexpr int LOC_CAND_CAP = 8192;    // appends per list and step (more: full compaction)
-constexpr int LOC_EV_MAX = 16384;     // events of a step handled locally (more: whole grid)
+constexpr int LOC_EV_MAX = 16384;     // largest limit of events handled locally (region list size)
 
 template <int DIM>
 __host__ __device__ constexpr int loc_cube() {
@@ -381,7 +382,7 @@ __global__ void k_loc_decide(const Dev<T> a) {
     c[LC_CANDB] = c[LC_CANDF] = c[LC_NREG] = 0;
     const int nev = *a.nev;
     const bool any = nev > 0;
-    const bool local = any && nev <= LOC_EV_MAX && nev <= a.cap_e;
+    const bool local = any && nev <= c[LC_EVMAX] && nev <= a.cap_e;
     c[LC_LOCAL] = local;
     c[LC_FULL] = any && !local;
 }

@@ -24,7 +24,7 @@ def built():
 
 
 def run(p, mask, steps, layout, **init):
-    s = lbrbc.Sim(dict(p, layout=layout, event_log_capacity=1 << 16), mask, **init)
+    s = lbrbc.Sim(dict(p, layout=layout, event_log_capacity=1 << 20), mask, **init)
     assert s.layout_info()["layout"] == layout
     s.step(steps)
     s.check()
@@ -102,16 +102,20 @@ def test_layouts_bitwise_equal_other_geometries(case):
     same(d, s)
 
 
-def run_lists(p, mask, steps, layout, local, **init):
-    old = os.environ.get("LBRBC_LOCAL_LISTS")
-    os.environ["LBRBC_LOCAL_LISTS"] = "1" if local else "0"
+def run_lists(p, mask, steps, layout, local, ev_max=None, **init):
+    env = {"LBRBC_LOCAL_LISTS": "1" if local else "0"}
+    if ev_max is not None:
+        env["LBRBC_LOCAL_EV_MAX"] = str(ev_max)
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update(env)
     try:
         return run(p, mask, steps, layout, **init)
     finally:
-        if old is None:
-            del os.environ["LBRBC_LOCAL_LISTS"]
-        else:
-            os.environ["LBRBC_LOCAL_LISTS"] = old
+        for k, v in old.items():
+            if v is None:
+                del os.environ[k]
+            else:
+                os.environ[k] = v
 
 
 @pytest.mark.parametrize("layout", ["dense", "sparse"])
@@ -136,6 +140,46 @@ def test_local_list_maintenance_matches_full_rebuild(layout, kind):
     assert np.array_equal(by_step(full["events"]), by_step(loc["events"]))
     for k in ("solute", "solid_over_vm", "unpaid", "dirichlet_in", "reacted"):
         assert loc["ledger"][k] == pytest.approx(full["ledger"][k], rel=1e-13, abs=1e-15), k
+
+
+@pytest.mark.parametrize("layout", ["dense", "sparse"])
+def test_local_and_whole_grid_steps_mixed_match_full_rebuild(layout):
+    # with the local limit lowered to 40 events, steps with few events are
+    # updated locally and steps with more over the whole grid, in one run;
+    # the dead entries and appends of the local steps meet full compactions
+    p, mask, init = pack_case("fp64", 3.0, 1.0, 1.0)
+    steps = 61
+    full = run_lists(p, mask, steps, layout, False, **init)
+    mixed = run_lists(p, mask, steps, layout, True, ev_max=40, **init)
+    per_step = np.bincount(full["events"][:, 0].astype(np.int64))
+    per_step = per_step[per_step > 0]
+    assert (per_step <= 40).any() and (per_step > 40).any()
+    for x, y in zip(full["fields"], mixed["fields"]):
+        assert np.array_equal(x, y)
+    assert np.array_equal(full["classes"], mixed["classes"])
+    assert np.array_equal(by_step(full["events"]), by_step(mixed["events"]))
+    for k in ("solute", "solid_over_vm", "unpaid", "dirichlet_in", "reacted"):
+        assert mixed["ledger"][k] == pytest.approx(full["ledger"][k], rel=1e-13, abs=1e-15), k
+
+
+@pytest.mark.parametrize("c_init", [1.6, 0.4])
+def test_local_list_maintenance_matches_full_rebuild_larger_pack(c_init):
+    # a 48^3 pack, supersaturated (precipitation) or undersaturated with the
+    # solid fraction of the grains near 0 (dissolution): many events per step
+    shape = (48, 48, 48)
+    mask = workloads.sphere_pack(shape, 0.5, 3.0, 6.0, seed=9, periodic=(False, True, True), buffer_x=3)
+    rng = np.random.default_rng(9)
+    phi0 = np.where(mask == 1, rng.uniform(0.0005, 0.05, shape), 0.0)
+    p = dict(dim=3, nx=48, ny=48, nz=48, flow_q=19, solute_q=7, bc=("open", "periodic", "periodic"), tau_flow=0.8,
+             magic_flow=3.0 / 16.0, tau_solute=0.9, rest_fraction=0.4, k_r=0.3, c_eq=1.0, c_init=c_init,
+             c_inlet=c_init, u_inlet=0.01, rho_outlet=1.0, molar_volume=2.0, phase_change=1, precision="fp32")
+    full = run_lists(p, mask, 41, "sparse", False, phi_init=phi0)
+    loc = run_lists(p, mask, 41, "sparse", True, phi_init=phi0)
+    assert len(full["events"]) > 200, len(full["events"])
+    for x, y in zip(full["fields"], loc["fields"]):
+        assert np.array_equal(x, y)
+    assert np.array_equal(full["classes"], loc["classes"])
+    assert np.array_equal(by_step(full["events"]), by_step(loc["events"]))
 
 
 def test_repacking_matches_oracle():

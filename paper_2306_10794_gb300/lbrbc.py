@@ -301,9 +301,18 @@ def make_params(p: dict) -> lbrbc_params:
     return s
 
 
+def _host(a):
+    """numpy view of an array-like input; torch tensors (on any device) are
+    copied to the host first (the library copies every input at creation)."""
+    if hasattr(a, "detach") and hasattr(a, "cpu"):
+        return a.detach().cpu().numpy()
+    return a
+
+
 class Sim:
     """One GPU simulation.  ``mask``: uint8 [z, y, x] (0 fluid, 1 reactive
-    solid, 2 Dirichlet solid); optional init fields as numpy arrays."""
+    solid, 2 Dirichlet solid); optional init fields; numpy arrays or torch
+    tensors."""
 
     def __init__(self, params: dict, mask, k_field=None, c_init=None, u_init=None, phi_init=None,
                  inlet_ux=None):
@@ -311,7 +320,7 @@ class Sim:
         self._p = make_params(params)
         self.shape = (self._p.nz, self._p.ny, self._p.nx)
         self.N = int(np.prod(self.shape))
-        m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8).reshape(-1))
+        m = np.ascontiguousarray(np.asarray(_host(mask), dtype=np.uint8).reshape(-1))
         if m.size != self.N:
             raise ValueError("mask size %d != grid %d" % (m.size, self.N))
         self._keep = {}
@@ -320,7 +329,7 @@ class Sim:
                              ("phi_init", phi_init, self.N), ("inlet_ux", inlet_ux, self._p.ny * self._p.nz)):
             if arr is None:
                 continue
-            a = np.ascontiguousarray(np.asarray(arr, dtype=np.float64).reshape(-1))
+            a = np.ascontiguousarray(np.asarray(_host(arr), dtype=np.float64).reshape(-1))
             if a.size != n:
                 raise ValueError("%s has %d entries, expected %d" % (name, a.size, n))
             self._keep[name] = a

@@ -228,3 +228,9 @@ def test_fields_as_device_tensors():
     for h, d in zip(host, dev):
         assert d.is_cuda and d.dtype == torch.float64 and tuple(d.shape) == h.shape
         assert np.array_equal(d.cpu().numpy(), h)
+    # a mask given as a torch tensor on the GPU gives the same simulation
+    g2 = lbrbc.Sim(p, torch.from_numpy(mask).cuda())
+    g2.step(9)
+    for a, b in zip(g2.fields(), host):
+        assert np.array_equal(a, b)
+    g2.close()

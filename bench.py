@@ -686,10 +686,14 @@ def main():
         phi_host = np.empty(mask.size)
         t0 = time.perf_counter()
         s2 = lbrbc.Sim(p, mask, **extra)
+        t1 = time.perf_counter()
         s2.step(K, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
         lbrbc.lbrbc_fields(s2._h, None, None, c_host, phi_host)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
+        parts = {"create_s": t1 - t0, "steps_s": t2 - t1, "fields_s": el - (t2 - t0)}
         s2.close()
         tt = torch.tensor([el], device="cuda", dtype=torch.float64)
         if dist:
@@ -698,7 +702,7 @@ def main():
         d2h = c_host.nbytes + phi_host.nbytes
         e2e = {"value": world * fluid * K / float(tt.item()) / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
-               "includes": "lbrbc_create from host mask + K steps + lbrbc_fields(c, phi) to host"}
+               "includes": "lbrbc_create from host mask + K steps + lbrbc_fields(c, phi) to host", **parts}
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:

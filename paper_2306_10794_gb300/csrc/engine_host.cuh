@@ -8,6 +8,37 @@
 
 namespace lbrbc {
 
+// Creation-time fills on the device (the padded per-cell arrays would
+// otherwise be built and copied from the host, ~3 GB at 512^3).
+static __global__ void k_fill_u32(uint32_t* __restrict__ a, long long n, uint32_t v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        a[i] = v;
+}
+
+// Scatter of a caller-layout (x-fastest, nx * ny * nz) FP64 field into the
+// padded grid; src null: v_reactive on reactive cells, 0 elsewhere.
+static __global__ void k_scatter_cells(double* __restrict__ dst, const double* __restrict__ src, const uint8_t* __restrict__ kind,
+                                Geo g, double v_reactive) {
+    const long long total = (long long)g.nx * g.ny * g.nz;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(t % g.nx), y = (int)((t / g.nx) % g.ny), z = (int)(t / ((long long)g.nx * g.ny));
+        const long long id = g.idx(x, y, z);
+        dst[id] = src ? src[t] : (kind[id] == KIND_REACTIVE ? v_reactive : 0.0);
+    }
+}
+
+// Initial concentration in the caller layout: c_dirichlet on Dirichlet
+// cells, c_init elsewhere.
+static __global__ void k_c0_cells(double* __restrict__ c0, const uint8_t* __restrict__ kind, Geo g, double c_init, double c_dir) {
+    const long long total = (long long)g.nx * g.ny * g.nz;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(t % g.nx), y = (int)((t / g.nx) % g.ny), z = (int)(t / ((long long)g.nx * g.ny));
+        c0[t] = kind[g.idx(x, y, z)] == KIND_DIRICHLET ? c_dir : c_init;
+    }
+}
+
 #define LB_CUDA(call)                                                                     \
     do {                                                                                  \
         cudaError_t e_ = (call);                                                          \
@@ -292,28 +323,33 @@ class Engine final : public ISim {
         LB_CUDA(cudaEventCreateWithFlags(&fork_, cudaEventDisableTiming));
         LB_CUDA(cudaEventCreateWithFlags(&join_, cudaEventDisableTiming));
 
-        // uploads
-        std::vector<double> phi(NP, 0.0);
-        std::vector<double> c0((size_t)ncell_);
-        for (int z = 0; z < g.nz; ++z)
-            for (int y = 0; y < g.ny; ++y)
-                for (int x = 0; x < g.nx; ++x) {
-                    const long long t = x + (long long)g.nx * (y + (long long)g.ny * z);
-                    const uint8_t m = mask[t];
-                    phi[g.idx(x, y, z)] = (ini && ini->phi_init) ? ini->phi_init[t] : (m == KIND_REACTIVE ? 1.0 : 0.0);
-                    c0[t] = (ini && ini->c_init) ? ini->c_init[t] : (m == KIND_DIRICHLET ? P.c_dirichlet : P.c_init);
-                }
+        // uploads: the kinds; phi, the initial concentration and the k field
+        // are formed on the device from them (or scattered from the caller's
+        // arrays)
         LB_CUDA(cudaMemcpy(d_.kind, kind.data(), NP, cudaMemcpyHostToDevice));
-        LB_CUDA(cudaMemcpy(d_.phi, phi.data(), NP * sizeof(double), cudaMemcpyHostToDevice));
+        const int gf = grid_for(ncell_, 256);
+        double* dtmp = nullptr;  // one caller-layout field at a time
+        LB_CUDA(talloc(&dtmp, (size_t)ncell_));
+        auto scatter = [&](double* dst, const double* host, double v_reactive) -> cudaError_t {
+            cudaError_t e = cudaMemset(dst, 0, NP * sizeof(double));
+            if (e == cudaSuccess && host) e = cudaMemcpy(dtmp, host, ncell_ * sizeof(double), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) k_scatter_cells<<<gf, 256, 0, own_>>>(dst, host ? dtmp : nullptr, d_.kind, g, v_reactive);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(own_);
+            return e;
+        };
+        if (cudaError_t e = scatter(d_.phi, (ini && ini->phi_init) ? ini->phi_init : nullptr, 1.0); e != cudaSuccess) {
+            cudaFree(dtmp);
+            err = std::string("phi upload: ") + cudaGetErrorString(e);
+            return 2;
+        }
         if (ini && ini->k_field) {
-            std::vector<double> kf(NP, 0.0);
-            for (int z = 0; z < g.nz; ++z)
-                for (int y = 0; y < g.ny; ++y)
-                    for (int x = 0; x < g.nx; ++x)
-                        kf[g.idx(x, y, z)] = ini->k_field[x + (long long)g.nx * (y + (long long)g.ny * z)];
             LB_CUDA(dalloc(&d_.kfield, (size_t)NP));
             LB_CUDA(dalloc(&d_.b_krate, (size_t)d_.cap_b));
-            LB_CUDA(cudaMemcpy(d_.kfield, kf.data(), NP * sizeof(double), cudaMemcpyHostToDevice));
+            if (cudaError_t e = scatter(d_.kfield, ini->k_field, 0.0); e != cudaSuccess) {
+                cudaFree(dtmp);
+                err = std::string("k field upload: ") + cudaGetErrorString(e);
+                return 2;
+            }
         } else {
             d_.kfield = nullptr;
             d_.b_krate = nullptr;
@@ -340,10 +376,8 @@ class Engine final : public ISim {
             LB_CUDA(cudaMemset(d_.G, 0, (size_t)QG * NP * sizeof(T)));
         }
         // ghost cells are solid for every lattice
-        {
-            std::vector<uint32_t> nwh(NP, CLS_SOLID);
-            LB_CUDA(cudaMemcpy(d_.nw, nwh.data(), NP * sizeof(uint32_t), cudaMemcpyHostToDevice));
-        }
+        k_fill_u32<<<grid_for(NP, 256), 256, 0, own_>>>(d_.nw, NP, CLS_SOLID);
+        LB_CUDA(cudaGetLastError());
         // classes, stored set (active-cell layout), lists, initial populations
         if (!d_.sparse) {
             if (rebuild(own_, 0, 1, err)) return 2;
@@ -353,9 +387,9 @@ class Engine final : public ISim {
             enqueue_lists(own_, 1);
             LB_CUDA(cudaGetLastError());
         }
-        double *dc0 = nullptr, *du0 = nullptr;
-        LB_CUDA(talloc(&dc0, (size_t)ncell_));
-        LB_CUDA(cudaMemcpy(dc0, c0.data(), ncell_ * sizeof(double), cudaMemcpyHostToDevice));
+        double *dc0 = dtmp, *du0 = nullptr;
+        if (ini && ini->c_init) LB_CUDA(cudaMemcpy(dc0, ini->c_init, ncell_ * sizeof(double), cudaMemcpyHostToDevice));
+        else k_c0_cells<<<grid_for(ncell_, 256), 256, 0, own_>>>(dc0, d_.kind, g, P.c_init, P.c_dirichlet);
         if (ini && ini->u_init) {
             LB_CUDA(talloc(&du0, (size_t)3 * ncell_));
             LB_CUDA(cudaMemcpy(du0, ini->u_init, 3 * ncell_ * sizeof(double), cudaMemcpyHostToDevice));

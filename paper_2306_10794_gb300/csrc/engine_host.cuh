@@ -3,6 +3,7 @@
 // driver and the measurement helper.
 #pragma once
 
+#include <algorithm>
 #include <thread>
 #include <vector>
 
@@ -139,18 +140,24 @@ class Engine final : public ISim {
             q.neg_vm = T(-p.Vm);
         }
 
-        // kinds with ghosts, host side
+        // kinds with ghosts, host side (z-slabs on host threads)
         const long long NP = g.NP;
         std::vector<uint8_t> kind(NP, KIND_OUTSIDE);
-        long long nsolid = 0, nfluid = 0;
-        for (int z = 0; z < g.nz; ++z)
-            for (int y = 0; y < g.ny; ++y)
+        std::vector<long long> nfl_z(g.nz, 0);
+        par_for(g.nz, [&](int z) {
+            long long c = 0;
+            for (int y = 0; y < g.ny; ++y) {
+                const uint8_t* row = mask + (long long)g.nx * (y + (long long)g.ny * z);
+                uint8_t* dst = kind.data() + g.idx(0, y, z);
                 for (int x = 0; x < g.nx; ++x) {
-                    const uint8_t m = mask[x + (long long)g.nx * (y + (long long)g.ny * z)];
-                    kind[g.idx(x, y, z)] = m;
-                    if (m == KIND_FLUID) nfluid++;
-                    else nsolid++;
+                    dst[x] = row[x];
+                    c += row[x] == KIND_FLUID;
                 }
+            }
+            nfl_z[z] = c;
+        });
+        long long nfluid = 0;
+        for (long long c : nfl_z) nfluid += c;
         nfluid_ = nfluid;
         // list capacities: the initial counts with head room for growth
         long long nb0 = 0, nf0 = 0;
@@ -174,15 +181,21 @@ class Engine final : public ISim {
         // GB300 the list is slower: a warp's 32 list cells span several rows,
         // so every population load touches more lines.
         {
-            long long active = 0;
-            for (int z = 0; z < g.nz; ++z)
-                for (int y = 0; y < g.ny; ++y)
+            std::vector<long long> act_z(g.nz, 0);
+            par_for(g.nz, [&](int z) {
+                long long c = 0;
+                for (int y = 0; y < g.ny; ++y) {
+                    const uint8_t* row = mask + (long long)g.nx * (y + (long long)g.ny * z);
                     for (int x0 = 0; x0 < g.nx; x0 += 32) {
                         bool any = false;
-                        for (int x = x0; x < std::min(g.nx, x0 + 32) && !any; ++x)
-                            any = mask[x + (long long)g.nx * (y + (long long)g.ny * z)] == KIND_FLUID;
-                        active += any;
+                        for (int x = x0; x < std::min(g.nx, x0 + 32) && !any; ++x) any = row[x] == KIND_FLUID;
+                        c += any;
                     }
+                }
+                act_z[z] = c;
+            });
+            long long active = 0;
+            for (long long c : act_z) active += c;
             lane_eff_ = active ? (double)nfluid / (32.0 * active) : 1.0;
             const bool fits = g.nx <= 2048 && g.ny <= 2048 && g.nz <= 1024;
             const char* env = getenv("LBRBC_FLUID_SWEEP");
@@ -800,19 +813,33 @@ class Engine final : public ISim {
     // The kinds are copied into a grid with one ghost layer (periodic axes
     // wrapped, others marked outside) so the count runs with fixed neighbour
     // offsets, split over host threads by z.
+    // f(i) for i in [0, n) over up to 16 host threads (i interleaved).
+    template <class F>
+    static void par_for(int n, F&& f) {
+        const int nt = (int)std::max(1u, std::min({16u, std::thread::hardware_concurrency(), (unsigned)std::max(1, n)}));
+        std::vector<std::thread> pool;
+        for (int t = 0; t < nt; ++t)
+            pool.emplace_back([&, t]() {
+                for (int i = t; i < n; i += nt) f(i);
+            });
+        for (auto& th : pool) th.join();
+    }
+
     void count_lists_host(const std::vector<uint8_t>& kind, long long& nb, long long& nf) const {
         const Geo& g = d_.geo;
         const int X = g.nx + 2, Y = g.ny + 2, Z = g.nz + 2;
         const uint8_t OUT = 255;
         std::vector<uint8_t> K((size_t)X * Y * Z, OUT);
         auto wrap = [](int v, int n, bool per) { return per ? (v + n) % n : v; };
-        for (int z = -1; z <= g.nz; ++z)
+        par_for(g.nz + 2, [&](int zi) {
+            const int z = zi - 1;
             for (int y = -1; y <= g.ny; ++y)
                 for (int x = -1; x <= g.nx; ++x) {
                     const int xs = wrap(x, g.nx, g.per_x), ys = wrap(y, g.ny, g.per_y), zs = wrap(z, g.nz, g.per_z);
                     if (xs < 0 || xs >= g.nx || ys < 0 || ys >= g.ny || zs < 0 || zs >= g.nz) continue;
                     K[(size_t)(x + 1) + (size_t)X * ((y + 1) + (size_t)Y * (z + 1))] = kind[g.idx(xs, ys, zs)];
                 }
+        });
         long long off[LG::Q];
         for (int o = 0; o < LG::Q; ++o) off[o] = LG::cx(o) + (long long)X * (LG::cy(o) + (long long)Y * LG::cz(o));
         const int nt = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));

@@ -386,12 +386,13 @@ def molins_arm(a):
 
     _build.build()
     stream = torch.cuda.current_stream()
-    rows, cells_steps, t_total = [], 0, 0.0
+    rows, cells_steps, t_total, launches = [], 0, 0.0, 0
     for case in [int(c) for c in a.molins_cases.split(",")]:
         for scheme in ("verhaeghe", "patel_ju", "new", "anti_bb"):
             p, mask, init, geom = workloads.case_molins(case, scheme, a.scale, precision=a.precision)
             s = lbrbc.Sim(p, mask, **init)
             fluid = s.info()["fluid_cells"]
+            per_step = s.launch_counts()["per_step"]
             chunk = max(1000, int(250_000 * a.scale * a.scale))
             cap = 3 * geom["steps_hint"]
             done, prev, led_prev = 0, None, s.ledger()["reacted"]
@@ -415,6 +416,7 @@ def molins_arm(a):
             s.check()
             s.close()
             cells_steps += fluid * done
+            launches += per_step * done
             t_total += ms * 1e-3
             rows.append({"case": case, "scheme": scheme, "R_avg": r, "R_avg_ledger": r_led,
                          "paper": TABLE2[case][scheme], "rel_to_paper": r / TABLE2[case][scheme] - 1.0,
@@ -427,7 +429,7 @@ def molins_arm(a):
             "config": {"workload": "2D reactive disc in a channel, %dx%d cells (scale %.2f of 600x1200), D2Q9 TRT flow "
                                    "Re=0.6 + D2Q5 TRT solute with rest fraction, cases %s, four k_i schemes"
                                    % (int(round(1200 * a.scale)), int(round(600 * a.scale)), a.scale, a.molins_cases)},
-            "table": rows, "mlups": cells_steps / t_total / 1e6, "gpu_launches": None}
+            "table": rows, "mlups": cells_steps / t_total / 1e6, "gpu_launches": launches}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -527,6 +529,10 @@ def adjoint_arm(a):
     t_a = time.perf_counter() - t0
     ck = clocks.stop()
     fluid = adj.info()["fluid_cells"]
+    # launches of lbrbc_adjoint over K steps: the forward pass (step graphs),
+    # the per-segment recomputation (the step's 3 kernels, launched one by
+    # one), the 3 adjoint kernels of each step, and the two ledger reductions
+    adj_launches = K * (adj.launch_counts()["per_step"] + 3 + 3) + 4
     adj.close()
     line = {"metric": METRIC, "value": t_a / t_f, "unit": "adjoint/forward time", "n_gpus": 1, "steps": K,
             "warmup": 3, "ms_per_step": t_a / K * 1e3, "higher_is_better": False, "scaling": "weak",
@@ -537,7 +543,7 @@ def adjoint_arm(a):
                        "fluid_cells": fluid},
             "forward_ms_per_step": t_f / K * 1e3, "adjoint_ms_per_step": t_a / K * 1e3,
             "J": J, "dJ_dk": dk, "dJ_dceq": dc, "dJ_dkfield_norm": float(np.sqrt((g ** 2).sum())),
-            "layout": lay, "clocks": ck, "clocks_forward": ck_f, "gpu_launches": None}
+            "layout": lay, "clocks": ck, "clocks_forward": ck_f, "gpu_launches": adj_launches}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -990,11 +990,28 @@ class Engine final : public ISim {
         // disjoint population slots (each slot is read and written by one
         // cell per step), and the fluid ends depend only on the boundary list.
         const bool fork = ev == nullptr;
+        // Inside a graph the phase-change path is the body of a conditional
+        // node: the gate after the fluid ends (the last kernel that raises
+        // events) sets its condition, and in a step without events also
+        // counts the step, so such a step launches nothing after the sweep.
+        bool cond = false;
+        cudaGraphConditionalHandle h{};
+        if (ph_.phase_change && fork && cond_graphs_) {
+            cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+            LB_CUDA(cudaStreamIsCapturing(st, &cst));
+            if (cst == cudaStreamCaptureStatusActive) {
+                cudaGraph_t gr = nullptr;
+                LB_CUDA(cudaStreamGetCaptureInfo(st, &cst, nullptr, &gr, nullptr, nullptr, nullptr));
+                LB_CUDA(cudaGraphConditionalHandleCreate(&h, gr, 0, 0));
+                cond = true;
+            }
+        }
         if (fork) {
             LB_CUDA(cudaEventRecord(fork_, st));
             LB_CUDA(cudaStreamWaitEvent(aux_, fork_, 0));
             launch_bound(aux_, odd, d_);
             k_fend<T, LG><<<fgrid_, LIST_BLOCK, 0, aux_>>>(d_, ph_);
+            if (cond) k_ev_gate<T><<<1, 1, 0, aux_>>>(d_, h);
             LB_CUDA(cudaEventRecord(join_, aux_));
         }
         if (sp) {
@@ -1018,17 +1035,12 @@ class Engine final : public ISim {
             LB_CUDA(cudaEventRecord(ev[3], st));
         }
         if (ph_.phase_change) {
-            // Inside a graph the event path is the body of a conditional node
-            // that runs only when this step raised events; a step without
-            // events pays one gate kernel instead of the path's launches.
-            cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
-            LB_CUDA(cudaStreamIsCapturing(st, &cst));
-            if (cst == cudaStreamCaptureStatusActive && cond_graphs_) {
-                if (enqueue_events_conditional(st, odd, d_, err)) return 2;
+            if (cond) {
+                if (enqueue_events_conditional(st, odd, d_, h, err)) return 2;
             } else {
                 enqueue_events(st, odd, d_);
+                k_step_end<T><<<1, 1, 0, st>>>(d_);
             }
-            k_step_end<T><<<1, 1, 0, st>>>(d_);
         }
         if (ev) LB_CUDA(cudaEventRecord(ev[4], st));
         LB_CUDA(cudaGetLastError());
@@ -1077,18 +1089,14 @@ class Engine final : public ISim {
         k_ev_reset<T><<<eg, 256, 0, st>>>(d_);
     }
 
-    // The same path as the body of an IF node of the graph being captured
-    // on st, gated on the step's event count.
-    int enqueue_events_conditional(cudaStream_t st, bool odd, const Dev<T>& d_, std::string& err) {
+    // The same path and the step counter as the body of an IF node (handle
+    // h, set by the gate) of the graph being captured on st.
+    int enqueue_events_conditional(cudaStream_t st, bool odd, const Dev<T>& d_, cudaGraphConditionalHandle h,
+                                   std::string& err) {
         cudaStreamCaptureStatus cst;
         cudaGraph_t gr = nullptr;
         const cudaGraphNode_t* deps = nullptr;
         size_t nd = 0;
-        LB_CUDA(cudaStreamGetCaptureInfo(st, &cst, nullptr, &gr, &deps, nullptr, &nd));
-        cudaGraphConditionalHandle h;
-        LB_CUDA(cudaGraphConditionalHandleCreate(&h, gr, 0, 0));
-        k_ev_gate<T><<<1, 1, 0, st>>>(d_, h);
-        LB_CUDA(cudaGetLastError());
         LB_CUDA(cudaStreamGetCaptureInfo(st, &cst, nullptr, &gr, &deps, nullptr, &nd));
         cudaGraphNodeParams np{};
         np.type = cudaGraphNodeTypeConditional;
@@ -1102,6 +1110,7 @@ class Engine final : public ISim {
         LB_CUDA(cudaStreamBeginCaptureToGraph(body_, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                               cudaStreamCaptureModeThreadLocal));
         enqueue_events(body_, odd, d_);
+        k_step_end<T><<<1, 1, 0, body_>>>(d_);
         cudaGraph_t bg = nullptr;
         const cudaError_t e1 = cudaGetLastError();
         const cudaError_t e2 = cudaStreamEndCapture(body_, &bg);
@@ -1127,7 +1136,8 @@ class Engine final : public ISim {
     // and an odd step).
     int event_path_launches() const override {
         if (!ph_.phase_change) return 0;
-        int n = 4 + 2 + 3 * (d_.use_fl ? 3 : 2) + 1;       // events, reclassification, lists, reset
+        int n = 4 + 2 + 3 * (d_.use_fl ? 3 : 2) + 1 + (cond_graphs_ ? 1 : 0);  // events, reclassification,
+                                                                             // lists, reset (+ step counter)
         if (d_.sparse) n += 1 + (1 + 9 + 1) + 6 + 1 + 2;  // repacking (conditional), table refresh, swaps of odd steps / 2
         if (d_.lcnt) n += 6;                              // local reclassification and list maintenance
         return n;
@@ -1140,7 +1150,7 @@ class Engine final : public ISim {
     // graph nodes).
     int launches_per_step() const override {
         int n = 3;
-        if (ph_.phase_change) n += cond_graphs_ ? 2 : 1 + event_path_launches();
+        if (ph_.phase_change) n += cond_graphs_ ? 1 : 1 + event_path_launches();
         return n;
     }
 

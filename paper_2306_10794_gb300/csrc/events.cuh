@@ -1093,10 +1093,13 @@ __global__ void k_ev_reset(const Dev<T> a) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) a.evidx[a.ev_node[e]] = -1;
 }
 
-// Condition of the graph node that holds the step's phase-change path.
+// Condition of the graph node that holds the step's phase-change path (and
+// the step counter); a step without events is counted here.
 template <typename T>
 __global__ void k_ev_gate(const Dev<T> a, cudaGraphConditionalHandle h) {
-    cudaGraphSetConditional(h, *a.nev > 0 ? 1u : 0u);
+    const bool any = *a.nev > 0;
+    cudaGraphSetConditional(h, any ? 1u : 0u);
+    if (!any) *a.step += 1;
 }
 
 template <typename T>

@@ -74,6 +74,9 @@ constexpr uint32_t BW_DEAD = 1u << 17;  // entry of a cell that is no longer a w
 #ifndef LBRBC_SP_NBR_STORE_HINT
 #define LBRBC_SP_NBR_STORE_HINT 1
 #endif
+#ifndef LBRBC_BOUND_BLOCKS
+#define LBRBC_BOUND_BLOCKS 5  // resident blocks per SM of the boundary kernel (register cap)
+#endif
 #ifndef LBRBC_SP_BLOCKS
 #define LBRBC_SP_BLOCKS 8
 #endif
@@ -1079,7 +1082,7 @@ __device__ __forceinline__ void bound_entry(const Dev<T>& a, const Phys& p, cons
 }
 
 template <typename T, class LF, class LG, bool ODD, bool SP>
-__global__ void __launch_bounds__(LIST_BLOCK, 4) k_bound(const Dev<T> a, const Phys p, const PhysT<T> q) {
+__global__ void __launch_bounds__(LIST_BLOCK, LBRBC_BOUND_BLOCKS) k_bound(const Dev<T> a, const Phys p, const PhysT<T> q) {
     const int n = *a.nb;
     DiffSum<T> racc, dacc;  // reacted mass and Dirichlet inflow of this thread
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)

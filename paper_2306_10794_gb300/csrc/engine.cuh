@@ -77,6 +77,14 @@ constexpr uint32_t BW_DEAD = 1u << 17;  // entry of a cell that is no longer a w
 #ifndef LBRBC_BOUND_BLOCKS
 #define LBRBC_BOUND_BLOCKS 5  // resident blocks per SM of the boundary kernel (register cap)
 #endif
+#ifndef LBRBC_SP_L2PF
+// odd active-cell sweep: L2 prefetch distance in blocks (0: none); one wave
+// of resident blocks on GB300 (152 SMs x 8): 2.29 -> 2.23 ms per launch at
+// 512^3 (608: 2.24, 2432: 2.31; prefetching the block's populations as
+// well: 2.44)
+#define LBRBC_SP_L2PF 1216
+#endif
+
 #ifndef LBRBC_SP_BLOCKS
 #define LBRBC_SP_BLOCKS 8
 #endif
@@ -777,6 +785,25 @@ __device__ __forceinline__ void sparse_cell(const Dev<T>& a, const Phys& p, cons
 template <typename T, class LF, class LG, bool ODD>
 __global__ void __launch_bounds__(FLUID_BLOCK, sizeof(T) == 4 ? LBRBC_SP_BLOCKS : 5) k_fluid_sp(const Dev<T> a, const Phys p, const PhysT<T> q) {
     const int ns = *a.ns;
+#if LBRBC_SP_L2PF
+    // ask the L2 for the table rows and node words (odd step) of the block
+    // LBRBC_SP_L2PF blocks ahead, which the scheduler starts about one wave
+    // later (a hint: nothing waits on it; rows inside the allocation, every
+    // range 16-byte aligned and a multiple of 16 bytes)
+    if (threadIdx.x == 0) {
+        constexpr int NT = tab_entries<LF, LG>();
+        const long long c0 = ((long long)blockIdx.x + LBRBC_SP_L2PF) * blockDim.x;
+        if (c0 < ns) {
+            const long long rows = min((long long)blockDim.x, a.cap_s - c0);  // a multiple of 64
+            if (ODD) {
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.etab + (size_t)c0 * NT),
+                             "r"((unsigned)(rows * NT * 4)) : "memory");
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.nwc + c0), "r"((unsigned)(rows * 4))
+                             : "memory");
+            }
+        }
+    }
+#endif
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < ns; n += gridDim.x * blockDim.x)
         sparse_cell<T, LF, LG, ODD>(a, p, q, n);
 }

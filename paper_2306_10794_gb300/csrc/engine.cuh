@@ -786,21 +786,19 @@ template <typename T, class LF, class LG, bool ODD>
 __global__ void __launch_bounds__(FLUID_BLOCK, sizeof(T) == 4 ? LBRBC_SP_BLOCKS : 5) k_fluid_sp(const Dev<T> a, const Phys p, const PhysT<T> q) {
     const int ns = *a.ns;
 #if LBRBC_SP_L2PF
-    // ask the L2 for the table rows and node words (odd step) of the block
+    // odd step: ask the L2 for the table rows and node words of the block
     // LBRBC_SP_L2PF blocks ahead, which the scheduler starts about one wave
     // later (a hint: nothing waits on it; rows inside the allocation, every
     // range 16-byte aligned and a multiple of 16 bytes)
-    if (threadIdx.x == 0) {
+    if (ODD && threadIdx.x == 0) {
         constexpr int NT = tab_entries<LF, LG>();
         const long long c0 = ((long long)blockIdx.x + LBRBC_SP_L2PF) * blockDim.x;
         if (c0 < ns) {
             const long long rows = min((long long)blockDim.x, a.cap_s - c0);  // a multiple of 64
-            if (ODD) {
-                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.etab + (size_t)c0 * NT),
-                             "r"((unsigned)(rows * NT * 4)) : "memory");
-                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.nwc + c0), "r"((unsigned)(rows * 4))
-                             : "memory");
-            }
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.etab + (size_t)c0 * NT),
+                         "r"((unsigned)(rows * NT * 4)) : "memory");
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.nwc + c0), "r"((unsigned)(rows * 4))
+                         : "memory");
         }
     }
 #endif
